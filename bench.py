@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark: deflated overlap propagator solve on one GB300.
+
+Workload (the paper's method at the size of its deflated-overlap runs, on
+synthetic inputs): 16^3 x 32 lattice, random SU(3) links U = exp(i 0.2 H)
+(seed 0) standing in for the paper's smeared 2+1-flavour ensemble, Wilson
+mass m0 = -1.5, sign(H_w) ~ Q P(Q^2) with the degree-527 Chebyshev
+approximation of x^{-1/2} on [4e-4, 1] (sqrt(eps) = 0.02, delta ~ 1e-10 by
+eq. 2), the 50 lowest |lambda| eigenvectors of Q treated exactly, quark mass
+0.02, one spin-colour point source solved to ||b - D x|| / ||b|| <= 1e-10.
+
+A step is one solve (every row of the hot path: Wilson kernels, Clenshaw
+polynomial, small-space projection, sign, D(m), chiral-sector CG in FP32
+with FP64 true-residual correction).  ``value`` counts D_ov applications
+(sign(H_w) applied to one right-hand side, any precision) per second
+sustained inside the timed solves.  Also reported: the FP64-only solve
+(time-to-solution against the mixed one), isolated FP32/FP64 D(m)
+applications, the Wilson-kernel bandwidth of the Clenshaw loops (roofline),
+and the CPU oracle's rate on a bounded sample.
+
+``--impl reference`` times the CPU oracle (the plain FP64 restatement of the
+method) on the same workload instead.  Multi-GPU runs (torchrun) are
+independent replicas: the method's solves do not shard here.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DIMS = (16, 16, 16, 32)
+LINK_EPS = 0.2
+M0 = -1.5
+SQRT_EPS = 0.02
+DEGREE = 527
+N_EV = 50
+MASS = 0.02
+TOL = 1e-10
+BC = (0, 0, 0, 1)  # periodic x, y, z; antiperiodic t
+METRIC = "D_ov applies/s, dslash HBM GB/s, time-to-1e-10 solve (mixed vs FP64)"
+UNIT = "D_ov applies/s"
+WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV}, m={MASS}, tol={TOL}"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(local_ms, local_units, world):
+    """Max of the step time and sum of the work over ranks (identity for one rank)."""
+    if world == 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+
+_ORACLE_INPUTS = {}
+
+
+def _oracle_inputs():
+    if not _ORACLE_INPUTS:
+        import numpy as np
+
+        import synth
+        from oracle import overlap as ov
+
+        U = synth.random_su3_field(DIMS, LINK_EPS, 0)
+        x = synth.gaussian_spinor(DIMS, 1, 1)[0]
+        rng = np.random.default_rng(3)
+        V = (rng.standard_normal((N_EV,) + x.shape) + 0j).astype(np.complex128)
+        _ORACLE_INPUTS.update(U=U, x=x, small=ov.SmallSpace(V, np.ones(N_EV)))
+    return _ORACLE_INPUTS
+
+
+def oracle_sample(n_wilson=4):
+    """Time the oracle's Wilson application at the workload size; return seconds per
+    D_ov application (2n + 1 Wilson applications plus the small-space projection)."""
+    from oracle import dirac
+    from oracle import overlap as ov
+
+    d = _oracle_inputs()
+    bcf = (1.0, 1.0, 1.0, -1.0)
+    t0 = time.perf_counter()
+    y = d["x"]
+    for _ in range(n_wilson):
+        y = dirac.hermitian_wilson(d["U"], y, M0, bcf)
+    t_w = (time.perf_counter() - t0) / n_wilson
+    t0 = time.perf_counter()
+    ov.project(d["small"], d["x"])
+    t_p = time.perf_counter() - t0
+    return (2 * DEGREE + 1) * t_w + t_p, t_w
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # every step: one bounded sample (2 oracle Wilson applications = one Y of the polynomial)
+    for _ in range(args.warmup):
+        oracle_sample(2)
+    t0 = time.perf_counter()
+    per_apply = []
+    for _ in range(args.steps):
+        pa, _ = oracle_sample(2)
+        per_apply.append(pa)
+    wall = time.perf_counter() - t0
+    t_apply = sum(per_apply) / len(per_apply)
+    value = 1.0 / t_apply
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "precision": "FP64 CPU oracle (numpy)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: 2 oracle H_w applications at 16^3x32 plus one 50-vector projection, "
+                                   f"scaled to {2 * DEGREE + 1} Wilson applications per D_ov application"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64-solve", action="store_true", help="skip the FP64-only comparison solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_1111_6288_gb300 as P
+
+    if not os.path.exists(P.library_path()):
+        from paper_1111_6288_gb300 import build as _b
+
+        _b.build()
+    import synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    U = torch.from_numpy(synth.random_su3_field(DIMS, LINK_EPS, 0)).to(dev)
+    common = dict(dims=DIMS, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE, max_nrhs=2)
+    ctx_mix = P.Context(P.Params(precision=P.OV_PREC_F32, inner_precision=P.OV_PREC_F32, **common))
+    ctx_64 = P.Context(P.Params(precision=P.OV_PREC_F64, inner_precision=P.OV_PREC_F64, **common))
+    ctx_mix.set_gauge(U)
+    ctx_64.set_gauge(U)
+    t0 = time.perf_counter()
+    lam, V = P.eigensolve_Q(ctx_64, N_EV, tol=1e-10, max_iter=200, register=True, want_vectors=True)
+    t_eig = time.perf_counter() - t0
+    P.deflate(ctx_mix, V, lam)
+    del V
+    # replicas solve different spin-colour point sources
+    sc = (rank % 4, (rank // 4) % 3)
+    b = torch.from_numpy(synth.point_sources(DIMS, [sc])).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(ctx):
+        flush.zero_()
+        x.zero_()
+        return P.solve_overlap(ctx, b, x, MASS, tol=TOL)
+
+    for _ in range(args.warmup):
+        step(ctx_mix)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K mixed-precision solves ----
+    ctx_mix.read_profile(P.OV_PREC_F32)
+    ctx_mix.read_profile(P.OV_PREC_F64)
+    ctx_mix.set_profiling(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = P.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [step(ctx_mix) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = P.launch_count() - launches0
+    barrier(world)
+    clk = clocks.stop()
+    ctx_mix.set_profiling(False)
+    prof32 = ctx_mix.read_profile(P.OV_PREC_F32)
+    prof64 = ctx_mix.read_profile(P.OV_PREC_F64)
+    local_ms = ev0.elapsed_time(ev1)
+    applies = float(sum(s.sign_applies for s in stats))
+    max_ms, total_applies = aggregate(local_ms, applies, world)
+    value = total_applies / (max_ms / 1e3)
+    worst_res = max(s.true_residual for s in stats)
+
+    # ---- end to end: host (pinned) b in, host x out, through the public API ----
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_applies = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        b.copy_(b_host, non_blocking=True)
+        x.zero_()
+        st = P.solve_overlap(ctx_mix, b, x, MASS, tol=TOL)
+        x_host.copy_(x, non_blocking=True)
+        e2e_applies += st.sign_applies
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms, e2e_total = aggregate(e0.elapsed_time(e1), e2e_applies, world)
+    nbytes = b.numel() * b.element_size()
+
+    # ---- isolated operator applications ----
+    def dov_rate(ctx, reps):
+        xi = b.to(ctx.spinor_dtype())
+        yi = torch.empty_like(xi)
+        P.apply_overlap(ctx, xi, yi, mass=MASS)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            P.apply_overlap(ctx, xi, yi, mass=MASS)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return reps / (a0.elapsed_time(a1) / 1e3)
+
+    rate32 = dov_rate(ctx_mix, 5)
+    rate64 = dov_rate(ctx_64, 2)
+
+    # ---- FP64-only solve (time-to-solution comparison) ----
+    fp64 = None
+    if not args.no_fp64_solve:
+        flush.zero_()
+        x.zero_()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        st64 = P.solve_overlap(ctx_64, b, x, MASS, tol=TOL)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"seconds": f0.elapsed_time(f1) / 1e3, "outer_iters": st64.outer_iters,
+                "inner_iters": st64.inner_iters, "sign_applies": st64.sign_applies,
+                "true_residual": st64.true_residual}
+
+    # ---- roofline of the dominant kernel: the FP32 Wilson kernel of the Clenshaw loops ----
+    peak, peak_kind = measured_peaks()
+    achieved = prof32["clenshaw_bytes"] / (prof32["clenshaw_ms"] / 1e3) / 1e9 if prof32["clenshaw_ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_kind,
+                "kernel": "dslash_kernel<float> (Clenshaw step launches, 16^3x32, 1-2 systems per launch)",
+                "avg_launch_us": 1e3 * prof32["clenshaw_ms"] / max(prof32["clenshaw_launches"], 1),
+                "bytes_per_launch": prof32["clenshaw_bytes"] / max(prof32["clenshaw_launches"], 1),
+                "clenshaw_share_of_step": prof32["clenshaw_ms"] / local_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_apply, t_w = oracle_sample(4)
+        cpu = {"value": 1.0 / t_apply, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"4 oracle H_w applications at 16^3x32 ({t_w:.2f} s each) plus one 50-vector projection, "
+                         f"scaled to {2 * DEGREE + 1} Wilson applications per D_ov application"}
+
+    if rank == 0:
+        mean_mixed_s = max_ms / 1e3 / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "links": f"exp(i {LINK_EPS} H), seed 0",
+                       "m0": M0, "poly_degree": DEGREE, "sqrt_eps": SQRT_EPS, "n_ev": N_EV, "mass": MASS,
+                       "tol": TOL, "precision": "FP32 inner CG and Clenshaw, FP64 true residual and update",
+                       "parallelism": f"replicas x{world}", "l2": "256 MB flush before every step"},
+            "time_to_solution": {"mixed_s": mean_mixed_s, "fp64_s": fp64["seconds"] if fp64 else None,
+                                 "speedup": (fp64["seconds"] / mean_mixed_s) if fp64 else None,
+                                 "mixed_outer_iters": stats[0].outer_iters, "mixed_inner_iters": stats[0].inner_iters,
+                                 "mixed_true_residual": worst_res, "fp64": fp64},
+            "dov_apply_per_s": {"f32": rate32, "f64": rate64},
+            "dslash_gbs": achieved,
+            "roofline": roofline,
+            "clocks": clk,
+            "e2e": {"value": e2e_total / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "setup": {"eigensolver_s": t_eig, "hw_norm": ctx_mix.hw_norm, "lambda_min": float(abs(lam).min()),
+                      "lambda_max_in_bank": float(abs(lam).max())},
+        }
+        print(json.dumps(line))
+    ctx_mix.close()
+    ctx_64.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

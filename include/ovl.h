@@ -1,0 +1,211 @@
+/*
+ * ovl.h -- C ABI of libovl, a single-GPU (GB300, sm_103a) implementation of
+ * the overlap Dirac operator and its propagator solve.
+ *
+ * Method (Lujan, Alexandru, Lee, "Electric polarizability of hadrons with
+ * overlap fermions on multi-GPUs", Lattice 2011):
+ *   Sec. 2, eq. 1   D_ov = 1 + gamma5 sign(H_w),  H_w = gamma5 D_w;
+ *   Sec. 2          sign(H_w) ~ Q P(Q^2) on the large space, Q = H_w/||H_w||,
+ *                   P a degree-n polynomial approximating x^{-1/2} on [eps, 1];
+ *                   exact on the small space spanned by low eigenvectors of Q;
+ *   Sec. 2, eq. 2   delta = |1 - sqrt(x) P(x)| ~ A exp(-b n sqrt(eps));
+ *   Sec. 3.2        CG for D^{-1} psi, single precision late in the solve;
+ *   Sec. 4          background field: U_mu -> exp(-i q A_mu) U_mu, Dirichlet
+ *                   boundaries in the field direction and in time.
+ *
+ * Conventions (the paper does not fix them):
+ *   D_w psi(n) = (4 + m0) psi(n) - 1/2 sum_mu [(1 - gamma_mu) U_mu(n) psi(n+mu)
+ *                                           + (1 + gamma_mu) U_mu(n-mu)^+ psi(n-mu)]
+ *   Euclidean chiral basis, gamma5 = diag(1, 1, -1, -1); mu = 0..3 is x, y, z, t.
+ *   The field phase is exp(i phi t) on x links, phi = q E, t = 0..Lt-1.
+ *   Massive operator D(m) = (1 - m/2) D_ov + m.
+ *   P(x) = sum_k c_k T_k(y), y = (2x - 1 - eps)/(1 - eps), c_0 already halved.
+ *
+ * Layouts (ABI; "site" = ((t*Lz + z)*Ly + y)*Lx + x, x fastest):
+ *   gauge   U[4][site][3][3]           complex (row a, column b)
+ *   spinor  psi[nrhs][site][4][3]      complex (spin, colour)
+ *   bank    V[n_ev][site][4][3]        complex
+ *   complex = interleaved (re, im); complex128 (dtype OV_C128) or complex64 (OV_C64).
+ *
+ * Memory: every pointer named "device" is a CUDA device pointer owned by the
+ * caller; the library never frees it and does not keep it after the call
+ * returns (it copies what it needs).  Host pointers are marked "host".  The
+ * library owns its internal copies (packed links, eigenvector banks,
+ * workspaces) and frees them in ov_destroy.
+ *
+ * Streams: every call takes a cudaStream_t (0 = legacy default stream) and
+ * enqueues its work on it.  apply_* and deflate return once the work is
+ * enqueued; solve_overlap, ov_eigensolve_Q and ov_estimate_hw_norm read
+ * scalars back and so synchronise the stream.  A context is not thread-safe.
+ *
+ * Errors: every int-returning call returns OV_OK or one of OV_ERR_*;
+ * ov_last_error(ctx) gives a message for the last failure on that context.
+ * Invalid sizes, pointers or states are rejected on the host before any
+ * launch.
+ */
+#ifndef OVL_H
+#define OVL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ov_stream_t; /* = cudaStream_t */
+typedef struct ov_ctx ov_ctx;
+
+enum {
+    OV_OK = 0,
+    OV_ERR_ARG = 1,           /* invalid argument (size, pointer, enum, alias) */
+    OV_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    OV_ERR_OOM = 3,           /* device allocation failed */
+    OV_ERR_NOT_CONVERGED = 4, /* iteration cap reached; outputs hold the best iterate */
+    OV_ERR_BREAKDOWN = 5,     /* CG breakdown: <p, A p> <= 0 */
+    OV_ERR_NAN = 6,           /* NaN or Inf met in a reduction */
+    OV_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
+    OV_ERR_NO_BANK = 8,       /* no small-space bank registered for a phase */
+    OV_ERR_STATE = 9          /* call out of order (e.g. no gauge field set) */
+};
+
+enum { OV_BC_PERIODIC = 0, OV_BC_ANTIPERIODIC = 1, OV_BC_DIRICHLET = 2 };
+
+/* Arithmetic of operator applications. F64: FP64 storage and arithmetic.
+ * F32: FP32 storage and arithmetic (reductions accumulate in FP64). */
+enum { OV_PREC_F64 = 0, OV_PREC_F32 = 1 };
+
+/* Element type of caller arrays. */
+enum { OV_C128 = 0, OV_C64 = 1 };
+
+typedef struct ov_params {
+    int dims[4];          /* Lx, Ly, Lz, Lt; each >= 2 */
+    int bc[4];            /* OV_BC_* per direction */
+    double m0;            /* Wilson mass in D_w (negative, e.g. -1.5, for overlap) */
+    double hw_norm;       /* ||H_w|| used for Q = H_w/hw_norm; <= 0 selects the bound
+                             |4 + m0| + 4, which is >= the spectral norm for any links */
+    double eps;           /* Q^2 interval [eps, 1] of the polynomial, 0 < eps < 1 */
+    int poly_degree;      /* n >= 1 */
+    const double* coeffs; /* host [n+1] coefficients of P in the T_k basis, or NULL for the
+                             Chebyshev interpolant of x^{-1/2} (see ov_chebyshev_coeffs) */
+    int precision;        /* OV_PREC_* of apply_wilson / apply_sign_Hw / apply_overlap */
+    int inner_precision;  /* OV_PREC_* of the inner CG in solve_overlap (FP64 outer loop) */
+    int max_nrhs;         /* largest nrhs of any call, >= 1 */
+    int max_iter;         /* cap on inner CG iterations per solve (<= 0: 100000) */
+    double inner_tol;     /* relative tolerance of each inner solve (<= 0: default,
+                             1e-5 for F32, 0.1 * tol for F64) */
+} ov_params;
+
+/* Per-solve statistics, filled on the host when solve_overlap returns. */
+typedef struct ov_solve_stats {
+    int status;             /* OV_OK / OV_ERR_* of the solve */
+    int outer_iters;        /* FP64 true-residual (defect-correction) cycles */
+    int inner_iters;        /* inner CG iterations, summed over cycles */
+    long long sign_applies; /* sign(H_w) applications, summed over right-hand sides */
+    long long dslash_calls; /* Wilson-operator applications, summed over right-hand sides */
+    double true_residual;   /* max over rhs of ||b - D(m) x|| / ||b||, FP64 operator */
+    double seconds;         /* wall time of the solve */
+} ov_solve_stats;
+
+/* Timing of the polynomial (Clenshaw) loops, the Wilson-kernel hot loop of every sign
+ * application, recorded with CUDA events on the call's stream while profiling is on. */
+typedef struct ov_profile {
+    double clenshaw_ms;          /* summed event time of the recorded loops */
+    long long clenshaw_regions;  /* loops recorded (one per sign application call) */
+    long long clenshaw_launches; /* Wilson-kernel launches inside them */
+    double clenshaw_bytes;       /* algorithmic bytes of those launches: per launch and site,
+                                    the 4 links once plus every input, output and epilogue
+                                    spinor of each system */
+    long long kernel_launches;   /* ov_launch_count() at the time of reading */
+} ov_profile;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context for one lattice geometry and operator parameter set.
+ * Copies *p (and p->coeffs).  Returns OV_ERR_ARG for invalid parameters. */
+int ov_create(const ov_params* p, ov_ctx** out);
+int ov_destroy(ov_ctx* ctx);
+/* Message of the last failure on ctx (or of the last ov_create failure if ctx is NULL). */
+const char* ov_last_error(const ov_ctx* ctx);
+/* Number of lattice sites. */
+long long ov_volume(const ov_ctx* ctx);
+/* ||H_w|| in use (after the hw_norm <= 0 default is resolved). */
+double ov_hw_norm(const ov_ctx* ctx);
+
+/* Turn event timing of the polynomial loops on (on != 0) or off. */
+int ov_set_profiling(ov_ctx* ctx, int on);
+/* Synchronise the events recorded for loops of the given precision (OV_PREC_*), sum them
+ * into *out and reset that record. */
+int ov_read_profile(ov_ctx* ctx, int precision, ov_profile* out);
+/* Kernels launched by the library so far (all contexts). */
+long long ov_launch_count(void);
+
+/* Copy the gauge field (device, [4][site][3][3], dtype OV_C128 or OV_C64) into the
+ * context's packed storage (FP64 and FP32 copies).  The caller may free U after
+ * the stream reaches this point.  Sec. 2 (D_w), Sec. 4 (links). */
+int ov_set_gauge(ov_ctx* ctx, const void* U, int dtype, ov_stream_t stream);
+
+/* Chebyshev coefficients the library uses when coeffs == NULL: the interpolant of
+ * x^{-1/2} on [eps, 1] at the n + 1 Chebyshev-Gauss nodes (Sec. 2). out: host [n+1]. */
+int ov_chebyshev_coeffs(int n, double eps, double* out);
+
+/* Eigen-decomposition of a small Hermitian matrix on the host (cyclic Jacobi), the
+ * routine the library uses for its Rayleigh-Ritz and Gram matrices.  A: host, n x n
+ * column-major complex128 (overwritten); w: host [n] eigenvalues ascending; Z: host
+ * n x n column-major complex128 eigenvectors (A = Z diag(w) Z^+).  No GPU needed. */
+int ov_host_eigh(int n, double* A, double* w, double* Z);
+
+/* ---- operator applications (Sec. 2) ------------------------------------ */
+
+/* out = D_w in (hermitian = 0) or H_w in = gamma5 D_w in (hermitian = 1).
+ * in, out: device spinors [nrhs][site][4][3], dtype OV_C128 if ctx precision is F64,
+ * OV_C64 if F32; in != out.  phase: host [nrhs] phi_j = q_j E_j (NULL = all zero). */
+int apply_wilson(ov_ctx* ctx, const void* in, void* out, int nrhs, const double* phase,
+                 int hermitian, ov_stream_t stream);
+
+/* out = sign(H_w) in ~ V diag(sign lambda) V^+ in + Q P(Q^2) (1 - V V^+) in, with the bank
+ * registered by deflate() for each phase (an empty small space when none is registered
+ * for phase 0; OV_ERR_NO_BANK for a non-zero phase without one).  Costs 2n + 1 Wilson
+ * applications.  Layout and dtype as apply_wilson. */
+int apply_sign_Hw(ov_ctx* ctx, const void* in, void* out, int nrhs, const double* phase,
+                  ov_stream_t stream);
+
+/* out = D(m) in = (1 - m/2)(in + gamma5 sign(H_w) in) + m in  (eq. 1; mass = 0: D_ov). */
+int apply_overlap(ov_ctx* ctx, const void* in, void* out, int nrhs, double mass,
+                  const double* phase, ov_stream_t stream);
+
+/* ---- small space (Sec. 2) ---------------------------------------------- */
+
+/* Register the small-space bank for field phase `phase`: V (device, [n_ev][site][4][3],
+ * dtype OV_C128 or OV_C64) and lambda (host [n_ev], eigenvalues of Q; only their signs
+ * are used, sign(0) = +1).  The library copies V, re-orthonormalises it in FP64
+ * (Cholesky QR, twice) and keeps an FP64 and an FP32 copy.  n_ev = 0 clears the bank.
+ * Replaces an earlier bank for the same phase. */
+int deflate(ov_ctx* ctx, double phase, const void* V, const double* lambda, int n_ev,
+            int dtype, ov_stream_t stream);
+
+/* Compute the n_ev eigenpairs of Q (FP64) of smallest |lambda| at field phase `phase` by
+ * Chebyshev-filtered subspace iteration with Rayleigh-Ritz, to residual
+ * ||Q v - lambda v|| <= tol.  V_out: device [n_ev][site][4][3] complex128 (may be NULL
+ * to only register); lambda_out: host [n_ev] (ascending |lambda|).  If register_bank is
+ * non-zero the result is also registered as by deflate().  Returns OV_ERR_NOT_CONVERGED
+ * (with the best vectors written) after max_iter filter cycles. */
+int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_iter,
+                    void* V_out, double* lambda_out, int register_bank, ov_stream_t stream);
+
+/* ---- propagator solve (Sec. 3.2) --------------------------------------- */
+
+/* Solve D(m) x = b for nrhs right-hand sides to ||b - D(m) x|| / ||b|| <= tol, with D(m)
+ * the FP64 operator apply_overlap computes.  b, x: device [nrhs][site][4][3] complex128;
+ * x is the initial guess on input and the solution on output; b != x.
+ * phase: host [nrhs] (NULL = all zero).  Outer loop: FP64 true residual and FP64 update
+ * of x.  Inner loop: CG in ctx inner_precision on the chiral-sector normal operator
+ * P_s [2(1 - m^2/4)(1 + s sign(H_w)) + m^2] P_s (one sign application per iteration and
+ * sector), then the correction D(m)^+ y.  stats: host, may be NULL. */
+int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, void* x,
+                  int nrhs, double tol, ov_solve_stats* stats, ov_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OVL_H */

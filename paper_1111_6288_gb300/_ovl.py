@@ -1,0 +1,366 @@
+"""ctypes binding of libovl (see include/ovl.h for the contract of each call)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libovl.so")
+
+OV_OK = 0
+OV_BC_PERIODIC, OV_BC_ANTIPERIODIC, OV_BC_DIRICHLET = 0, 1, 2
+OV_PREC_F64, OV_PREC_F32 = 0, 1
+OV_C128, OV_C64 = 0, 1
+ERROR_NAMES = {1: "ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN", 6: "NAN", 7: "TIMEOUT",
+               8: "NO_BANK", 9: "STATE"}
+
+
+class OvlError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"libovl error {code} ({ERROR_NAMES.get(code, '?')}): {message}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("dims", C.c_int * 4),
+        ("bc", C.c_int * 4),
+        ("m0", C.c_double),
+        ("hw_norm", C.c_double),
+        ("eps", C.c_double),
+        ("poly_degree", C.c_int),
+        ("coeffs", C.POINTER(C.c_double)),
+        ("precision", C.c_int),
+        ("inner_precision", C.c_int),
+        ("max_nrhs", C.c_int),
+        ("max_iter", C.c_int),
+        ("inner_tol", C.c_double),
+    ]
+
+
+class _SolveStats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int),
+        ("outer_iters", C.c_int),
+        ("inner_iters", C.c_int),
+        ("sign_applies", C.c_longlong),
+        ("dslash_calls", C.c_longlong),
+        ("true_residual", C.c_double),
+        ("seconds", C.c_double),
+    ]
+
+
+class _Profile(C.Structure):
+    _fields_ = [
+        ("clenshaw_ms", C.c_double),
+        ("clenshaw_regions", C.c_longlong),
+        ("clenshaw_launches", C.c_longlong),
+        ("clenshaw_bytes", C.c_double),
+        ("kernel_launches", C.c_longlong),
+    ]
+
+
+_VP, _DP, _I, _D = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double
+
+_SIGNATURES = {
+    "ov_create": (_I, [C.POINTER(_Params), C.POINTER(_VP)]),
+    "ov_destroy": (_I, [_VP]),
+    "ov_last_error": (C.c_char_p, [_VP]),
+    "ov_volume": (C.c_longlong, [_VP]),
+    "ov_hw_norm": (_D, [_VP]),
+    "ov_set_gauge": (_I, [_VP, _VP, _I, _VP]),
+    "ov_set_profiling": (_I, [_VP, _I]),
+    "ov_read_profile": (_I, [_VP, _I, C.POINTER(_Profile)]),
+    "ov_launch_count": (C.c_longlong, []),
+    "ov_chebyshev_coeffs": (_I, [_I, _D, _DP]),
+    "ov_host_eigh": (_I, [_I, _DP, _DP, _DP]),
+    "apply_wilson": (_I, [_VP, _VP, _VP, _I, _DP, _I, _VP]),
+    "apply_sign_Hw": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
+    "apply_overlap": (_I, [_VP, _VP, _VP, _I, _D, _DP, _VP]),
+    "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
+    "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
+    "solve_overlap": (_I, [_VP, _D, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def lib():
+    """The loaded libovl.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libovl.so is not built ({_LIB_PATH}); run paper_1111_6288_gb300.build.build()")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, ctx_handle=None):
+    if rc != OV_OK:
+        msg = lib().ov_last_error(ctx_handle)
+        raise OvlError(rc, msg.decode() if msg else "")
+
+
+def _darr(values):
+    if values is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+    return a, a.ctypes.data_as(_DP)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Params:
+    """Mirror of ``ov_params`` (include/ovl.h)."""
+
+    dims: Sequence[int]
+    bc: Sequence[int] = (OV_BC_PERIODIC, OV_BC_PERIODIC, OV_BC_PERIODIC, OV_BC_ANTIPERIODIC)
+    m0: float = -1.5
+    hw_norm: float = 0.0
+    eps: float = 0.01
+    poly_degree: int = 200
+    coeffs: Optional[Sequence[float]] = None
+    precision: int = OV_PREC_F64
+    inner_precision: int = OV_PREC_F64
+    max_nrhs: int = 12
+    max_iter: int = 0
+    inner_tol: float = 0.0
+
+
+@dataclass
+class SolveStats:
+    status: int = 0
+    outer_iters: int = 0
+    inner_iters: int = 0
+    sign_applies: int = 0
+    dslash_calls: int = 0
+    true_residual: float = 0.0
+    seconds: float = 0.0
+
+
+class Context:
+    """An ``ov_ctx``: one lattice geometry and operator parameter set."""
+
+    def __init__(self, params: Params):
+        p = _Params()
+        p.dims[:] = list(params.dims)
+        p.bc[:] = list(params.bc)
+        p.m0 = params.m0
+        p.hw_norm = params.hw_norm
+        p.eps = params.eps
+        p.poly_degree = params.poly_degree
+        self._coeffs, cptr = _darr(params.coeffs)
+        p.coeffs = cptr
+        p.precision = params.precision
+        p.inner_precision = params.inner_precision
+        p.max_nrhs = params.max_nrhs
+        p.max_iter = params.max_iter
+        p.inner_tol = params.inner_tol
+        h = C.c_void_p()
+        rc = lib().ov_create(C.byref(p), C.byref(h))
+        _check(rc, None)
+        self.handle = h
+        self.params = params
+        self.dims = tuple(int(d) for d in params.dims)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ov_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def volume(self):
+        return int(lib().ov_volume(self.handle))
+
+    @property
+    def hw_norm(self):
+        return float(lib().ov_hw_norm(self.handle))
+
+    @property
+    def site_shape(self):
+        lx, ly, lz, lt = self.dims
+        return (lt, lz, ly, lx)
+
+    def spinor_dtype(self):
+        import torch
+
+        return torch.complex128 if self.params.precision == OV_PREC_F64 else torch.complex64
+
+    def _check_spinor(self, t, name, dtype=None):
+        import torch
+
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        want = dtype or self.spinor_dtype()
+        if t.dtype != want:
+            raise TypeError(f"{name} has dtype {t.dtype}, expected {want}")
+        if tuple(t.shape[1:]) != self.site_shape + (4, 3):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected (nrhs,) + {self.site_shape + (4, 3)}")
+        return t.shape[0]
+
+    def set_profiling(self, on=True):
+        """Record CUDA events around every polynomial (Clenshaw) loop."""
+        _check(lib().ov_set_profiling(self.handle, int(on)), self.handle)
+
+    def read_profile(self, precision=OV_PREC_F32):
+        """Summed event time, launches and algorithmic bytes of the recorded loops of one
+        precision (resets them)."""
+        p = _Profile()
+        _check(lib().ov_read_profile(self.handle, int(precision), C.byref(p)), self.handle)
+        return dict(clenshaw_ms=p.clenshaw_ms, clenshaw_regions=p.clenshaw_regions,
+                    clenshaw_launches=p.clenshaw_launches, clenshaw_bytes=p.clenshaw_bytes,
+                    kernel_launches=p.kernel_launches)
+
+    def set_gauge(self, U, stream=None):
+        import torch
+
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.is_contiguous()):
+            raise TypeError("U must be a contiguous CUDA tensor")
+        if tuple(U.shape) != (4,) + self.site_shape + (3, 3):
+            raise ValueError(f"U has shape {tuple(U.shape)}")
+        dt = {torch.complex128: OV_C128, torch.complex64: OV_C64}.get(U.dtype)
+        if dt is None:
+            raise TypeError("U must be complex128 or complex64")
+        _check(lib().ov_set_gauge(self.handle, C.c_void_p(U.data_ptr()), dt, _stream(stream)), self.handle)
+
+
+def _phase_ptr(phase, nrhs):
+    if phase is None:
+        return None, None
+    if np.isscalar(phase):
+        phase = [float(phase)] * nrhs
+    if len(phase) != nrhs:
+        raise ValueError("phase must have one entry per right-hand side")
+    return _darr(phase)
+
+
+def apply_wilson(ctx: Context, x, out, phase=None, hermitian=False, stream=None):
+    """out = D_w x (or H_w x = gamma5 D_w x if hermitian)."""
+    n = ctx._check_spinor(x, "x")
+    ctx._check_spinor(out, "out")
+    keep, ph = _phase_ptr(phase, n)
+    rc = lib().apply_wilson(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, ph, int(hermitian),
+                            _stream(stream))
+    _check(rc, ctx.handle)
+    return out
+
+
+def apply_sign_Hw(ctx: Context, x, out, phase=None, stream=None):
+    """out = sign(H_w) x with the registered small space."""
+    n = ctx._check_spinor(x, "x")
+    ctx._check_spinor(out, "out")
+    keep, ph = _phase_ptr(phase, n)
+    _check(lib().apply_sign_Hw(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, ph,
+                               _stream(stream)), ctx.handle)
+    return out
+
+
+def apply_overlap(ctx: Context, x, out, mass=0.0, phase=None, stream=None):
+    """out = D(m) x = (1 - m/2)(x + gamma5 sign(H_w) x) + m x."""
+    n = ctx._check_spinor(x, "x")
+    ctx._check_spinor(out, "out")
+    keep, ph = _phase_ptr(phase, n)
+    _check(lib().apply_overlap(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, float(mass), ph,
+                               _stream(stream)), ctx.handle)
+    return out
+
+
+def deflate(ctx: Context, V, lam, phase=0.0, stream=None):
+    """Register the small-space bank (V: [n_ev, ...site..., 4, 3] CUDA tensor, lam: n_ev eigenvalues of Q)."""
+    import torch
+
+    lam_a, lam_p = _darr(lam)
+    n_ev = 0 if lam_a is None else len(lam_a)
+    if n_ev == 0:
+        _check(lib().deflate(ctx.handle, float(phase), None, None, 0, OV_C128, _stream(stream)), ctx.handle)
+        return
+    dt = {torch.complex128: OV_C128, torch.complex64: OV_C64}.get(V.dtype)
+    if dt is None or not V.is_cuda or not V.is_contiguous() or V.shape[0] != n_ev:
+        raise TypeError("V must be a contiguous CUDA complex tensor with one vector per eigenvalue")
+    ctx._check_spinor(V, "V", dtype=V.dtype)
+    _check(lib().deflate(ctx.handle, float(phase), C.c_void_p(V.data_ptr()), lam_p, n_ev, dt, _stream(stream)),
+           ctx.handle)
+
+
+def eigensolve_Q(ctx: Context, n_ev, phase=0.0, tol=1e-10, max_iter=100, register=True, want_vectors=False,
+                 stream=None):
+    """Lowest-|lambda| eigenpairs of Q (FP64); returns (lambda, V or None)."""
+    import torch
+
+    lam = np.zeros(n_ev)
+    V = None
+    vptr = None
+    if want_vectors:
+        V = torch.empty((n_ev,) + ctx.site_shape + (4, 3), dtype=torch.complex128, device="cuda")
+        vptr = C.c_void_p(V.data_ptr())
+    rc = lib().ov_eigensolve_Q(ctx.handle, float(phase), int(n_ev), float(tol), int(max_iter), vptr,
+                               lam.ctypes.data_as(_DP), int(register), _stream(stream))
+    _check(rc, ctx.handle)
+    return lam, V
+
+
+def solve_overlap(ctx: Context, b, x, mass, tol=1e-10, phase=None, stream=None, raise_on_error=True):
+    """Solve D(m) x = b (x: initial guess in, solution out); returns SolveStats."""
+    import torch
+
+    n = ctx._check_spinor(b, "b", dtype=torch.complex128)
+    ctx._check_spinor(x, "x", dtype=torch.complex128)
+    keep, ph = _phase_ptr(phase, n)
+    st = _SolveStats()
+    rc = lib().solve_overlap(ctx.handle, float(mass), ph, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), n,
+                             float(tol), C.byref(st), _stream(stream))
+    stats = SolveStats(st.status, st.outer_iters, st.inner_iters, st.sign_applies, st.dslash_calls, st.true_residual,
+                       st.seconds)
+    if raise_on_error:
+        _check(rc, ctx.handle)
+    return stats
+
+
+def launch_count():
+    """Kernels the library has launched so far in this process."""
+    return int(lib().ov_launch_count())
+
+
+def chebyshev_coeffs(n, eps):
+    """The library's Chebyshev coefficients of x^{-1/2} on [eps, 1] (host; no GPU)."""
+    out = np.zeros(n + 1)
+    _check(lib().ov_chebyshev_coeffs(int(n), float(eps), out.ctypes.data_as(_DP)))
+    return out
+
+
+def host_eigh(A):
+    """The library's host Hermitian eigensolver (no GPU); returns (w ascending, Z)."""
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128)).copy(order="F")
+    n = A.shape[0]
+    w = np.zeros(n)
+    Z = np.zeros((n, n), dtype=np.complex128, order="F")
+    _check(lib().ov_host_eigh(n, A.ctypes.data_as(_DP), w.ctypes.data_as(_DP), Z.ctypes.data_as(_DP)))
+    return w, Z

@@ -1,0 +1,1130 @@
+// libovl C ABI: context, operator applications, small space, solver, eigensolver.
+//
+// Host orchestration of the kernels in dslash.cu and blas.cu.  Paper mapping:
+//   apply_wilson          Sec. 2, H_w = gamma5 D_w
+//   apply_sign_Hw         Sec. 2, sign(H_w) ~ V diag(s) V^+ + Q P(Q^2)(1 - V V^+)
+//   apply_overlap         Sec. 2, eq. 1, D_ov = 1 + gamma5 sign(H_w); D(m) = (1 - m/2) D_ov + m
+//   deflate               Sec. 2, small space from eigenvectors of Q
+//   ov_eigensolve_Q       Sec. 3.1, low eigenmodes of H_w with Chebyshev acceleration
+//   solve_overlap         Sec. 3.2, CG for D^{-1} psi, single precision late in the solve
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/ovl.h"
+#include "ovl_internal.h"
+
+using namespace ovl;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Bank {
+    double phase = 0.0;
+    int n = 0;
+    void* V64 = nullptr;  // [n][12][V] double2
+    void* V32 = nullptr;  // [n][12][V] float2
+    double* d_signs = nullptr;  // [n]
+    std::vector<double> signs;
+};
+
+struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ov_ctx {
+    Geom g;
+    ov_params p;
+    std::vector<double> coeffs;
+    double hw_norm = 0.0;
+    std::string err;
+    void* U64 = nullptr;
+    void* U32 = nullptr;
+    bool gauge_set = false;
+    std::vector<Bank> banks;
+    std::map<std::string, Buf> ws;
+    double2* d_partial = nullptr;
+    long long partial_cap = 0;
+    double2* d_red = nullptr;
+    double2* d_C = nullptr;   // small matrices [cap_c]
+    double2* d_C2 = nullptr;
+    long long cap_c = 0;
+    double* d_phase = nullptr;  // per-system phases
+    signed char* d_chi = nullptr;
+    int* d_idx = nullptr;
+    int cap_sys = 0;
+    long long dslash_count = 0;
+    long long sign_count = 0;
+    // optional CUDA-event timing of the Clenshaw loops (the Wilson kernels of the polynomial)
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[2];  // per OV_PREC_*
+    long long prof_launches[2] = {0, 0};
+    double prof_bytes[2] = {0.0, 0.0};
+};
+
+namespace {
+
+int fail(ov_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return fail(c, OV_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                           \
+    } while (0)
+#define CKL()                                                                                           \
+    do {                                                                                                \
+        cudaError_t e_ = cudaGetLastError();                                                            \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(c, OV_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__,    \
+                        __LINE__);                                                                      \
+    } while (0)
+#define TRY(x)                    \
+    do {                          \
+        int rc_ = (x);            \
+        if (rc_ != OV_OK) return rc_; \
+    } while (0)
+
+template <typename R>
+constexpr int prec_of() { return std::is_same<R, double>::value ? OV_PREC_F64 : OV_PREC_F32; }
+
+size_t vec_bytes(const ov_ctx* c, int prec) { return (size_t)12 * c->g.V * (prec == OV_PREC_F64 ? 16 : 8); }
+
+// Named workspace of at least nvec spinor vectors of the given precision.
+int workspace(ov_ctx* c, const std::string& name, int prec, long long nvec, void** out) {
+    const size_t need = vec_bytes(c, prec) * (size_t)std::max<long long>(nvec, 1);
+    const std::string key = name + (prec == OV_PREC_F64 ? "/64" : "/32");
+    Buf& b = c->ws[key];
+    if (b.bytes < need) {
+        if (b.ptr) {
+            CK(cudaDeviceSynchronize());
+            CK(cudaFree(b.ptr));
+            b.ptr = nullptr;
+            b.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&b.ptr, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, OV_ERR_OOM, "workspace '%s': cudaMalloc(%zu) failed: %s", key.c_str(), need,
+                        cudaGetErrorString(e));
+        }
+        b.bytes = need;
+    }
+    *out = b.ptr;
+    return OV_OK;
+}
+
+int ensure_small(ov_ctx* c, long long nmat, long long npartial, int nsys) {
+    if (nmat > c->cap_c) {
+        if (c->d_C) {
+            CK(cudaDeviceSynchronize());
+            CK(cudaFree(c->d_C));
+            CK(cudaFree(c->d_C2));
+        }
+        c->cap_c = std::max<long long>(nmat, 4096);
+        CK(cudaMalloc(&c->d_C, sizeof(double2) * c->cap_c));
+        CK(cudaMalloc(&c->d_C2, sizeof(double2) * c->cap_c));
+    }
+    if (npartial > c->partial_cap) {
+        if (c->d_partial) {
+            CK(cudaDeviceSynchronize());
+            CK(cudaFree(c->d_partial));
+        }
+        c->partial_cap = std::max<long long>(npartial, 1 << 20);
+        CK(cudaMalloc(&c->d_partial, sizeof(double2) * c->partial_cap));
+    }
+    if (nsys > c->cap_sys) {
+        if (c->d_phase) {
+            CK(cudaDeviceSynchronize());
+            CK(cudaFree(c->d_phase));
+            CK(cudaFree(c->d_chi));
+            CK(cudaFree(c->d_idx));
+            CK(cudaFree(c->d_red));
+        }
+        c->cap_sys = std::max(nsys, 64);
+        CK(cudaMalloc(&c->d_phase, sizeof(double) * c->cap_sys));
+        CK(cudaMalloc(&c->d_chi, c->cap_sys));
+        CK(cudaMalloc(&c->d_idx, sizeof(int) * 2 * c->cap_sys));
+        CK(cudaMalloc(&c->d_red, sizeof(double2) * c->cap_sys));
+    }
+    return OV_OK;
+}
+
+Bank* find_bank(ov_ctx* c, double phase) {
+    for (auto& b : c->banks)
+        if (b.phase == phase) return &b;
+    return nullptr;
+}
+
+// ---- small kernels local to the orchestration --------------------------------
+
+__global__ void proj_coeff_k(const double2* __restrict__ C, const double* __restrict__ signs, int n, int k,
+                             double2* __restrict__ Cneg, double2* __restrict__ Cs) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int i = idx / k;
+    const double2 v = C[idx];
+    Cneg[idx] = make_double2(-v.x, -v.y);
+    Cs[idx] = make_double2(signs[i] * v.x, signs[i] * v.y);
+}
+
+template <typename R>
+__global__ void merge_sectors_k(const typename C2<R>::T* __restrict__ Y, const int* __restrict__ sys_of_rhs,
+                                typename C2<R>::T* __restrict__ out, long long n) {
+    const int j = blockIdx.y;
+    const int s0 = sys_of_rhs[2 * j], s1 = sys_of_rhs[2 * j + 1];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        typename C2<R>::T v;
+        v.x = 0;
+        v.y = 0;
+        if (s0 >= 0) {
+            typename C2<R>::T a = Y[(long long)s0 * n + i];
+            v.x += a.x;
+            v.y += a.y;
+        }
+        if (s1 >= 0) {
+            typename C2<R>::T a = Y[(long long)s1 * n + i];
+            v.x += a.x;
+            v.y += a.y;
+        }
+        out[(long long)j * n + i] = v;
+    }
+}
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void random_fill_k(double2* __restrict__ x, long long n, unsigned long long seed) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long a = splitmix64(seed ^ (2ULL * i)), b = splitmix64(seed ^ (2ULL * i + 1));
+        x[i] = make_double2((double)(a >> 11) * 0x1.0p-53 - 0.5, (double)(b >> 11) * 0x1.0p-53 - 0.5);
+    }
+}
+
+// ---- the sign pipeline ---------------------------------------------------------
+
+struct SysSet {
+    int n = 0;
+    std::vector<double> phase;       // [n]
+    std::vector<signed char> chi;    // [n] (may be empty)
+};
+
+int upload_sys(ov_ctx* c, const SysSet& S, cudaStream_t s) {
+    TRY(ensure_small(c, 0, 0, S.n));
+    CK(cudaMemcpyAsync(c->d_phase, S.phase.data(), sizeof(double) * S.n, cudaMemcpyHostToDevice, s));
+    if (!S.chi.empty()) CK(cudaMemcpyAsync(c->d_chi, S.chi.data(), S.n, cudaMemcpyHostToDevice, s));
+    return OV_OK;
+}
+
+bool any_phase(const SysSet& S) {
+    for (double p : S.phase)
+        if (p != 0.0) return true;
+    return false;
+}
+
+// out = Proj(G(c_op H_w P(Q^2) x_perp + c1 y_s)) + c2 v2 + c3 v3 over S.n systems of precision R,
+// where (y_s, x_perp) is the projection of (g5_in ? gamma5 X : X).  fin.v1 is set here.
+template <typename R>
+int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogue fin, void* out, cudaStream_t s) {
+    const int prec = prec_of<R>();
+    const int V = c->g.V;
+    const long long n12 = 12LL * V;
+    const int ns = S.n;
+    TRY(upload_sys(c, S, s));
+    const double* d_phase = any_phase(S) ? c->d_phase : nullptr;
+
+    void *xg, *xperp, *ys, *t, *bA, *bB;
+    TRY(workspace(c, "sp_xg", prec, ns, &xg));
+    TRY(workspace(c, "sp_xperp", prec, ns, &xperp));
+    TRY(workspace(c, "sp_ys", prec, ns, &ys));
+    TRY(workspace(c, "sp_t", prec, ns, &t));
+    TRY(workspace(c, "sp_bA", prec, ns, &bA));
+    TRY(workspace(c, "sp_bB", prec, ns, &bB));
+    const size_t es = sizeof(typename C2<R>::T);
+
+    const void* src = X;
+    if (g5_in) {
+        launch_gamma5<R>(X, xg, V, ns, s);
+        CKL();
+        src = xg;
+    }
+
+    // small space: runs of equal phase share a bank
+    bool any_bank = false;
+    for (int j0 = 0; j0 < ns;) {
+        int j1 = j0 + 1;
+        while (j1 < ns && S.phase[j1] == S.phase[j0]) ++j1;
+        const int k = j1 - j0;
+        Bank* b = find_bank(c, S.phase[j0]);
+        const char* src_j = (const char*)src + (size_t)j0 * n12 * es;
+        char* xp_j = (char*)xperp + (size_t)j0 * n12 * es;
+        char* ys_j = (char*)ys + (size_t)j0 * n12 * es;
+        if (!b && S.phase[j0] != 0.0)
+            return fail(c, OV_ERR_NO_BANK, "no small-space bank registered for phase %.17g", S.phase[j0]);
+        if (!b || b->n == 0) {
+            CK(cudaMemcpyAsync(xp_j, src_j, (size_t)k * n12 * es, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemsetAsync(ys_j, 0, (size_t)k * n12 * es, s));
+        } else {
+            any_bank = true;
+            const int N = b->n;
+            const void* Vb = std::is_same<R, double>::value ? b->V64 : b->V32;
+            TRY(ensure_small(c, 2LL * N * k, (long long)N * k * 4 * 152, ns));
+            multidot<R>(Vb, n12, N, src_j, n12, k, n12, c->d_C, c->d_partial, c->partial_cap, s);
+            CKL();
+            double2* Cneg = c->d_C2;
+            double2* Cs = c->d_C2 + (long long)N * k;
+            proj_coeff_k<<<(N * k + 127) / 128, 128, 0, s>>>(c->d_C, b->d_signs, N, k, Cneg, Cs);
+            count_launch();
+            CKL();
+            combine<R>(Vb, n12, N, Cneg, k, k, 1.0, src_j, n12, xp_j, n12, n12, s);
+            CKL();
+            combine<R>(Vb, n12, N, Cs, k, k, 0.0, nullptr, n12, ys_j, n12, n12, s);
+            CKL();
+        }
+        j0 = j1;
+    }
+
+    // Clenshaw recurrence for p = P(Q^2) x_perp, P = sum_k c_k T_k(Y),
+    // Y = (2 Q^2 - (1 + eps))/(1 - eps) = alpha H_w^2 + beta/2:
+    //   b_n = c_n x_perp;  b_k = c_k x_perp + 2 Y b_{k+1} - b_{k+2};
+    //   p = c_0 x_perp + Y b_1 - b_2.
+    const int n = c->p.poly_degree;
+    const double eps = c->p.eps, h = c->hw_norm;
+    const double alpha = 4.0 / ((1.0 - eps) * h * h);
+    const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
+    const double m0 = c->p.m0;
+    const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
+    launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, s);
+    CKL();
+    void* b1 = bA;
+    void* b2 = nullptr;
+    Epilogue plain;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->profile) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, s));
+    }
+    // algorithmic bytes per site of one launch: links once (shared by the systems) plus each
+    // system's input, output and epilogue vectors
+    const double esd = (double)sizeof(typename C2<R>::T), Vd = (double)V;
+    for (int k = n - 1; k >= 0; --k) {
+        if (c->profile) {
+            c->prof_bytes[prec] += Vd * esd * (36.0 + 24.0 * ns);                        // t = H_w b1
+            c->prof_bytes[prec] += Vd * esd * (36.0 + 12.0 * ns * (b2 ? 5.0 : 4.0));     // b_k
+            c->prof_launches[prec] += 2;
+        }
+        launch_dslash<R>(c->g, m0, U, b1, t, ns, d_phase, plain, s);
+        Epilogue e;
+        const double half = (k == 0) ? 0.5 : 1.0;
+        e.c_op = alpha * half;
+        e.c1 = beta * half;
+        e.v1 = b1;
+        e.c2 = c->coeffs[k];
+        e.v2 = xperp;
+        e.c3 = -1.0;
+        e.v3 = b2;
+        void* o = b2 ? b2 : bB;
+        launch_dslash<R>(c->g, m0, U, t, o, ns, d_phase, e, s);
+        b2 = b1;
+        b1 = o;
+    }
+    CKL();
+    if (c->profile) {
+        CK(cudaEventRecord(ev1, s));
+        c->prof_events[prec].emplace_back(ev0, ev1);
+    }
+    // b1 now holds p.  Final: out = Proj(G(c_op H_w p + c1 y_s)) + c2 v2 + c3 v3
+    fin.v1 = any_bank ? ys : nullptr;
+    launch_dslash<R>(c->g, m0, U, b1, out, ns, d_phase, fin, s);
+    CKL();
+    c->dslash_count += (long long)(2 * n + 1) * ns;
+    c->sign_count += ns;
+    return OV_OK;
+}
+
+// D(m) X (g5_in = false) or D(m)^+ X (g5_in = true) on internal vectors.
+template <typename R>
+int overlap_op(ov_ctx* c, const void* X, const SysSet& S, double mass, bool dagger, void* out, cudaStream_t s) {
+    Epilogue fin;
+    fin.c_op = (1.0 - 0.5 * mass) / c->hw_norm;
+    fin.c1 = 1.0 - 0.5 * mass;
+    fin.g5 = dagger ? 0 : 1;
+    fin.c2 = 1.0 + 0.5 * mass;
+    fin.v2 = X;
+    return sign_pipeline<R>(c, X, S, dagger, fin, out, s);
+}
+
+int check_ready(ov_ctx* c, const void* in, const void* out, int nrhs) {
+    if (!c) return OV_ERR_ARG;
+    if (!c->gauge_set) return fail(c, OV_ERR_STATE, "no gauge field set (call ov_set_gauge first)");
+    if (!in || !out) return fail(c, OV_ERR_ARG, "null spinor pointer");
+    if (in == out) return fail(c, OV_ERR_ARG, "in and out must be different buffers");
+    if (nrhs < 1 || nrhs > c->p.max_nrhs)
+        return fail(c, OV_ERR_ARG, "nrhs = %d outside [1, max_nrhs = %d]", nrhs, c->p.max_nrhs);
+    return OV_OK;
+}
+
+SysSet make_sys(int nrhs, const double* phase) {
+    SysSet S;
+    S.n = nrhs;
+    S.phase.assign(nrhs, 0.0);
+    if (phase)
+        for (int j = 0; j < nrhs; ++j) S.phase[j] = phase[j];
+    return S;
+}
+
+int phase_check(ov_ctx* c, const SysSet& S) {
+    for (double p : S.phase)
+        if (!std::isfinite(p)) return fail(c, OV_ERR_ARG, "non-finite phase");
+    return OV_OK;
+}
+
+template <typename R>
+int apply_generic(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, int kind, double mass,
+                  cudaStream_t s) {
+    const int prec = prec_of<R>();
+    const int dt = (prec == OV_PREC_F64) ? OV_C128 : OV_C64;
+    void *X, *Y;
+    TRY(workspace(c, "io_in", prec, nrhs, &X));
+    TRY(workspace(c, "io_out", prec, nrhs, &Y));
+    launch_pack_spinor<R>(in, dt, X, c->g.V, nrhs, s);
+    CKL();
+    SysSet S = make_sys(nrhs, phase);
+    TRY(phase_check(c, S));
+    if (kind == 0 || kind == 1) {  // D_w (0) or H_w (1)
+        TRY(upload_sys(c, S, s));
+        Epilogue e;
+        e.g5 = (kind == 0);  // gamma5 H_w = D_w
+        launch_dslash<R>(c->g, c->p.m0, std::is_same<R, double>::value ? c->U64 : c->U32, X, Y, nrhs,
+                         any_phase(S) ? c->d_phase : nullptr, e, s);
+        CKL();
+        c->dslash_count += nrhs;
+    } else if (kind == 2) {  // sign
+        Epilogue fin;
+        fin.c_op = 1.0 / c->hw_norm;
+        fin.c1 = 1.0;
+        TRY(sign_pipeline<R>(c, X, S, false, fin, Y, s));
+    } else {  // D(m)
+        TRY(overlap_op<R>(c, X, S, mass, false, Y, s));
+    }
+    launch_unpack_spinor<R>(Y, out, dt, c->g.V, nrhs, s);
+    CKL();
+    return OV_OK;
+}
+
+// ---- block helpers for orthonormalisation and Rayleigh-Ritz (FP64) ----------------
+
+// Gram matrix G = W^+ W (m x m) to host, column-major.
+int gram_host(ov_ctx* c, const void* A, int na, const void* B, int nb, std::vector<HostCplx>& H, cudaStream_t s) {
+    const long long n12 = 12LL * c->g.V;
+    TRY(ensure_small(c, (long long)na * nb, (long long)na * nb * 4 * 152, 1));
+    multidot<double>(A, n12, na, B, n12, nb, n12, c->d_C, c->d_partial, c->partial_cap, s);
+    CKL();
+    std::vector<double2> tmp((size_t)na * nb);
+    CK(cudaMemcpyAsync(tmp.data(), c->d_C, sizeof(double2) * na * nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    H.assign((size_t)na * nb, HostCplx{0, 0});
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) H[i + (size_t)j * na] = HostCplx{tmp[(size_t)i * nb + j].x, tmp[(size_t)i * nb + j].y};
+    return OV_OK;
+}
+
+// out_j = sum_i A_i M(i, j), M column-major na x nb on the host.
+int rotate(ov_ctx* c, const void* A, int na, const std::vector<HostCplx>& M, int nb, void* out, cudaStream_t s) {
+    const long long n12 = 12LL * c->g.V;
+    TRY(ensure_small(c, (long long)na * nb, 0, 1));
+    std::vector<double2> tmp((size_t)na * nb);
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) tmp[(size_t)i * nb + j] = make_double2(M[i + (size_t)j * na].re, M[i + (size_t)j * na].im);
+    CK(cudaMemcpyAsync(c->d_C, tmp.data(), sizeof(double2) * na * nb, cudaMemcpyHostToDevice, s));
+    combine<double>(A, n12, na, c->d_C, nb, nb, 0.0, nullptr, n12, out, n12, n12, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    return OV_OK;
+}
+
+void hermitize(std::vector<HostCplx>& T, int n) {
+    for (int i = 0; i < n; ++i) {
+        T[i + (size_t)i * n].im = 0.0;
+        for (int j = 0; j < i; ++j) {
+            HostCplx& x = T[i + (size_t)j * n];
+            HostCplx& y = T[j + (size_t)i * n];
+            const double re = 0.5 * (x.re + y.re), im = 0.5 * (x.im - y.im);
+            x = HostCplx{re, im};
+            y = HostCplx{re, -im};
+        }
+    }
+}
+
+// Cholesky-QR, twice: W (m vectors, FP64) <- W R with W^+ W = 1.  tmp: m vectors.
+int cholqr2(ov_ctx* c, void* W, int m, void* tmp, cudaStream_t s) {
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<HostCplx> G, Rm;
+        TRY(gram_host(c, W, m, W, m, G, s));
+        hermitize(G, m);
+        if (!host_cholesky(m, G)) return fail(c, OV_ERR_BREAKDOWN, "Cholesky-QR: Gram matrix not positive definite");
+        host_inv_lower_dag(m, G, Rm);
+        TRY(rotate(c, W, m, Rm, m, tmp, s));
+        CK(cudaMemcpyAsync(W, tmp, vec_bytes(c, OV_PREC_F64) * m, cudaMemcpyDeviceToDevice, s));
+    }
+    return OV_OK;
+}
+
+int register_bank_internal(ov_ctx* c, double phase, const void* W64, int n, const double* lam, cudaStream_t s) {
+    Bank* b = find_bank(c, phase);
+    if (!b) {
+        c->banks.push_back(Bank());
+        b = &c->banks.back();
+        b->phase = phase;
+    }
+    if (b->V64) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaFree(b->V64));
+        CK(cudaFree(b->V32));
+        CK(cudaFree(b->d_signs));
+        b->V64 = b->V32 = nullptr;
+        b->d_signs = nullptr;
+    }
+    b->n = n;
+    b->signs.assign(n, 1.0);
+    if (n == 0) return OV_OK;
+    for (int i = 0; i < n; ++i) b->signs[i] = (lam[i] >= 0.0) ? 1.0 : -1.0;
+    const size_t b64 = vec_bytes(c, OV_PREC_F64) * n, b32 = vec_bytes(c, OV_PREC_F32) * n;
+    if (cudaMalloc(&b->V64, b64) != cudaSuccess || cudaMalloc(&b->V32, b32) != cudaSuccess ||
+        cudaMalloc(&b->d_signs, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "bank allocation of %d vectors failed", n);
+    }
+    CK(cudaMemcpy(b->d_signs, b->signs.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(b->V64, W64, b64, cudaMemcpyDeviceToDevice, s));
+    launch_convert<double, float>(b->V64, b->V32, 12LL * c->g.V * n, s);
+    CKL();
+    return OV_OK;
+}
+
+// Chebyshev filter W <- T_d(Z) W (then normalised by the caller), Z = (2 Q^2 - (1 + a))/(1 - a),
+// which damps the part of the spectrum of Q^2 in [a, 1] and amplifies [0, a).  W is FP64;
+// the recurrence runs in precision R.
+template <typename R>
+int cheb_filter(ov_ctx* c, void* W64, int m, double a, int degree, const double* d_phase, cudaStream_t s) {
+    const int prec = prec_of<R>();
+    const long long n = 12LL * c->g.V * m;
+    const size_t vb = vec_bytes(c, prec);
+    void *W, *Tm, *Tc, *tt;
+    if (std::is_same<R, double>::value) {
+        W = W64;
+    } else {
+        TRY(workspace(c, "flt_W", prec, m, &W));
+        launch_convert<double, float>(W64, W, n, s);
+        CKL();
+    }
+    TRY(workspace(c, "flt_Tm", prec, m, &Tm));
+    TRY(workspace(c, "flt_Tc", prec, m, &Tc));
+    TRY(workspace(c, "flt_t", prec, m, &tt));
+    const double h = c->hw_norm, m0 = c->p.m0;
+    const double za = 2.0 / ((1.0 - a) * h * h), zb = -(1.0 + a) / (1.0 - a);
+    const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
+    Epilogue plain;
+    launch_dslash<R>(c->g, m0, U, W, tt, m, d_phase, plain, s);
+    Epilogue e1;
+    e1.c_op = za;
+    e1.c1 = zb;
+    e1.v1 = W;
+    launch_dslash<R>(c->g, m0, U, tt, Tc, m, d_phase, e1, s);  // T_1 = Z W
+    CK(cudaMemcpyAsync(Tm, W, vb * m, cudaMemcpyDeviceToDevice, s));  // T_0
+    void* tk = Tc;
+    void* tkm = Tm;
+    for (int k = 1; k < degree; ++k) {
+        launch_dslash<R>(c->g, m0, U, tk, tt, m, d_phase, plain, s);
+        Epilogue e;
+        e.c_op = 2.0 * za;
+        e.c1 = 2.0 * zb;
+        e.v1 = tk;
+        e.c3 = -1.0;
+        e.v3 = tkm;
+        launch_dslash<R>(c->g, m0, U, tt, tkm, m, d_phase, e, s);  // T_{k+1} written over T_{k-1}
+        std::swap(tk, tkm);
+    }
+    CKL();
+    c->dslash_count += 2LL * degree * m;
+    if (std::is_same<R, double>::value) {
+        CK(cudaMemcpyAsync(W64, tk, vb * m, cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_convert<float, double>(tk, W64, n, s);
+        CKL();
+    }
+    return OV_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+int ov_create(const ov_params* p, ov_ctx** out) {
+    ov_ctx* c = nullptr;
+    if (!p || !out) return fail(c, OV_ERR_ARG, "null argument");
+    *out = nullptr;
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (p->dims[mu] < 2) return fail(c, OV_ERR_ARG, "dims[%d] = %d < 2", mu, p->dims[mu]);
+        if (p->bc[mu] < 0 || p->bc[mu] > 2) return fail(c, OV_ERR_ARG, "bc[%d] = %d invalid", mu, p->bc[mu]);
+        V *= p->dims[mu];
+    }
+    if (V > (1LL << 30) / 12) return fail(c, OV_ERR_ARG, "lattice too large for 32-bit site indexing");
+    if (!(p->eps > 0.0 && p->eps < 1.0)) return fail(c, OV_ERR_ARG, "eps = %g outside (0, 1)", p->eps);
+    if (p->poly_degree < 1 || p->poly_degree > 100000)
+        return fail(c, OV_ERR_ARG, "poly_degree = %d outside [1, 100000]", p->poly_degree);
+    if (p->precision != OV_PREC_F64 && p->precision != OV_PREC_F32)
+        return fail(c, OV_ERR_ARG, "precision = %d invalid", p->precision);
+    if (p->inner_precision != OV_PREC_F64 && p->inner_precision != OV_PREC_F32)
+        return fail(c, OV_ERR_ARG, "inner_precision = %d invalid", p->inner_precision);
+    if (p->max_nrhs < 1 || p->max_nrhs > kMaxRhs / 2)
+        return fail(c, OV_ERR_ARG, "max_nrhs = %d outside [1, %d]", p->max_nrhs, kMaxRhs / 2);
+    if (!std::isfinite(p->m0)) return fail(c, OV_ERR_ARG, "m0 not finite");
+    c = new ov_ctx();
+    c->p = *p;
+    for (int mu = 0; mu < 4; ++mu) {
+        c->g.L[mu] = p->dims[mu];
+        c->g.bcf[mu] = p->bc[mu] == OV_BC_PERIODIC ? 1.0 : (p->bc[mu] == OV_BC_ANTIPERIODIC ? -1.0 : 0.0);
+    }
+    c->g.V = (int)V;
+    c->coeffs.resize(p->poly_degree + 1);
+    if (p->coeffs) std::copy(p->coeffs, p->coeffs + p->poly_degree + 1, c->coeffs.begin());
+    else host_chebyshev_coeffs(p->poly_degree, p->eps, c->coeffs.data());
+    c->p.coeffs = nullptr;
+    c->hw_norm = p->hw_norm > 0.0 ? p->hw_norm : std::fabs(4.0 + p->m0) + 4.0;
+    if (c->p.max_iter <= 0) c->p.max_iter = 100000;
+    *out = c;
+    return OV_OK;
+}
+
+int ov_destroy(ov_ctx* c) {
+    if (!c) return OV_OK;
+    cudaDeviceSynchronize();
+    for (auto& kv : c->ws)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    for (auto& b : c->banks) {
+        if (b.V64) cudaFree(b.V64);
+        if (b.V32) cudaFree(b.V32);
+        if (b.d_signs) cudaFree(b.d_signs);
+    }
+    for (auto& v : c->prof_events)
+        for (auto& e : v) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    void* ps[] = {c->U64, c->U32, c->d_partial, c->d_red, c->d_C, c->d_C2, c->d_phase, c->d_chi, c->d_idx};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    delete c;
+    return OV_OK;
+}
+
+const char* ov_last_error(const ov_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+long long ov_volume(const ov_ctx* c) { return c ? c->g.V : 0; }
+
+double ov_hw_norm(const ov_ctx* c) { return c ? c->hw_norm : 0.0; }
+
+int ov_chebyshev_coeffs(int n, double eps, double* out) {
+    if (n < 0 || !out || !(eps > 0.0 && eps < 1.0)) return OV_ERR_ARG;
+    host_chebyshev_coeffs(n, eps, out);
+    return OV_OK;
+}
+
+int ov_host_eigh(int n, double* A, double* w, double* Z) {
+    if (n < 1 || !A || !w || !Z) return OV_ERR_ARG;
+    std::vector<HostCplx> M((size_t)n * n), Zm;
+    std::memcpy(M.data(), A, sizeof(HostCplx) * n * n);
+    std::vector<double> wv;
+    host_eigh(n, M, wv, Zm);
+    std::memcpy(w, wv.data(), sizeof(double) * n);
+    std::memcpy(Z, Zm.data(), sizeof(HostCplx) * n * n);
+    return OV_OK;
+}
+
+int ov_set_profiling(ov_ctx* c, int on) {
+    if (!c) return OV_ERR_ARG;
+    c->profile = on != 0;
+    return OV_OK;
+}
+
+int ov_read_profile(ov_ctx* c, int precision, ov_profile* out) {
+    if (!c || !out || (precision != OV_PREC_F64 && precision != OV_PREC_F32)) return OV_ERR_ARG;
+    const int p = precision;
+    double ms = 0.0;
+    for (auto& e : c->prof_events[p]) {
+        CK(cudaEventSynchronize(e.second));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e.first, e.second));
+        ms += t;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    out->clenshaw_ms = ms;
+    out->clenshaw_regions = (long long)c->prof_events[p].size();
+    out->clenshaw_launches = c->prof_launches[p];
+    out->clenshaw_bytes = c->prof_bytes[p];
+    out->kernel_launches = g_launches.load();
+    c->prof_events[p].clear();
+    c->prof_launches[p] = 0;
+    c->prof_bytes[p] = 0.0;
+    return OV_OK;
+}
+
+long long ov_launch_count(void) { return g_launches.load(); }
+
+int ov_set_gauge(ov_ctx* c, const void* U, int dtype, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    if (!U) return fail(c, OV_ERR_ARG, "null gauge pointer");
+    if (dtype != OV_C128 && dtype != OV_C64) return fail(c, OV_ERR_ARG, "dtype = %d invalid", dtype);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = 4ull * 9 * c->g.V;
+    if (!c->U64) {
+        if (cudaMalloc(&c->U64, n * sizeof(double2)) != cudaSuccess ||
+            cudaMalloc(&c->U32, n * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, OV_ERR_OOM, "gauge field allocation failed");
+        }
+    }
+    launch_pack_gauge<double>(U, dtype, c->U64, c->g.V, s);
+    launch_pack_gauge<float>(U, dtype, c->U32, c->g.V, s);
+    CKL();
+    c->gauge_set = true;
+    return OV_OK;
+}
+
+int apply_wilson(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, int hermitian,
+                 ov_stream_t stream) {
+    TRY(check_ready(c, in, out, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kind = hermitian ? 1 : 0;
+    return c->p.precision == OV_PREC_F64 ? apply_generic<double>(c, in, out, nrhs, phase, kind, 0.0, s)
+                                         : apply_generic<float>(c, in, out, nrhs, phase, kind, 0.0, s);
+}
+
+int apply_sign_Hw(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, ov_stream_t stream) {
+    TRY(check_ready(c, in, out, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->p.precision == OV_PREC_F64 ? apply_generic<double>(c, in, out, nrhs, phase, 2, 0.0, s)
+                                         : apply_generic<float>(c, in, out, nrhs, phase, 2, 0.0, s);
+}
+
+int apply_overlap(ov_ctx* c, const void* in, void* out, int nrhs, double mass, const double* phase,
+                  ov_stream_t stream) {
+    TRY(check_ready(c, in, out, nrhs));
+    if (!std::isfinite(mass)) return fail(c, OV_ERR_ARG, "mass not finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->p.precision == OV_PREC_F64 ? apply_generic<double>(c, in, out, nrhs, phase, 3, mass, s)
+                                         : apply_generic<float>(c, in, out, nrhs, phase, 3, mass, s);
+}
+
+int deflate(ov_ctx* c, double phase, const void* V, const double* lambda, int n_ev, int dtype, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_ev < 0 || n_ev > 384) return fail(c, OV_ERR_ARG, "n_ev = %d outside [0, 384]", n_ev);
+    if (n_ev > 0 && (!V || !lambda)) return fail(c, OV_ERR_ARG, "null V or lambda");
+    if (dtype != OV_C128 && dtype != OV_C64) return fail(c, OV_ERR_ARG, "dtype = %d invalid", dtype);
+    if (!std::isfinite(phase)) return fail(c, OV_ERR_ARG, "non-finite phase");
+    if (n_ev == 0) return register_bank_internal(c, phase, nullptr, 0, nullptr, s);
+    for (int i = 0; i < n_ev; ++i)
+        if (!std::isfinite(lambda[i])) return fail(c, OV_ERR_ARG, "lambda[%d] not finite", i);
+    void *W, *T;
+    TRY(workspace(c, "defl_W", OV_PREC_F64, n_ev, &W));
+    TRY(workspace(c, "defl_T", OV_PREC_F64, n_ev, &T));
+    launch_pack_spinor<double>(V, dtype, W, c->g.V, n_ev, s);
+    CKL();
+    TRY(cholqr2(c, W, n_ev, T, s));
+    return register_bank_internal(c, phase, W, n_ev, lambda, s);
+}
+
+int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter, void* V_out, double* lambda_out,
+                    int register_bank, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    if (!c->gauge_set) return fail(c, OV_ERR_STATE, "no gauge field set");
+    if (n_ev < 1 || n_ev > 200) return fail(c, OV_ERR_ARG, "n_ev = %d outside [1, 200]", n_ev);
+    if (!lambda_out) return fail(c, OV_ERR_ARG, "null lambda_out");
+    if (!(tol > 0.0)) return fail(c, OV_ERR_ARG, "tol must be > 0");
+    if (!std::isfinite(phase)) return fail(c, OV_ERR_ARG, "non-finite phase");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int m = std::min(std::min(n_ev + std::max(16, n_ev / 2), 12 * c->g.V), kMaxRhs);
+    const long long n12 = 12LL * c->g.V;
+    const size_t vb = vec_bytes(c, OV_PREC_F64);
+    void *W, *W2, *QW, *QW2, *tt;
+    TRY(workspace(c, "eig_W", OV_PREC_F64, m, &W));
+    TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
+    TRY(workspace(c, "eig_QW", OV_PREC_F64, m, &QW));
+    TRY(workspace(c, "eig_QW2", OV_PREC_F64, m, &QW2));
+    TRY(workspace(c, "eig_t", OV_PREC_F64, m, &tt));
+    random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)W, n12 * m, 0x5eed0f0e1ULL);
+    count_launch();
+    CKL();
+    TRY(cholqr2(c, W, m, W2, s));
+    SysSet S;
+    S.n = m;
+    S.phase.assign(m, phase);
+    TRY(upload_sys(c, S, s));
+    const double* d_phase = phase != 0.0 ? c->d_phase : nullptr;
+    const double h = c->hw_norm;
+    // The filter runs in FP32 while the residuals are far above FP32 resolution, then in FP64.
+    // Its degree is chosen each cycle so that the largest amplification, |T_d(z(0))| with
+    // z(0) = -(1 + a)/(1 - a), stays below amp: a larger spread between the filtered columns
+    // would collapse the block below the resolution of the Cholesky-QR step.
+    const double switch_res = 3e-5;
+    double a = -1.0;  // lower end of the damped interval of Q^2 (set by each Rayleigh-Ritz)
+    std::vector<double> theta(m), res(m, 1e300);
+    double worst = 1e300;
+    int status = OV_ERR_NOT_CONVERGED;
+    std::string hist;
+    for (int it = 0; it <= max_iter; ++it) {
+        if (it > 0) {
+            const bool lo = worst > switch_res;
+            const double amp = lo ? 1e3 : 1e6;
+            const double z0 = (1.0 + a) / (1.0 - a);
+            const int degree = std::max(2, std::min(200, (int)std::ceil(std::acosh(amp) / std::acosh(z0))));
+            if (lo) TRY(cheb_filter<float>(c, W, m, a, degree, d_phase, s));
+            else TRY(cheb_filter<double>(c, W, m, a, degree, d_phase, s));
+            TRY(cholqr2(c, W, m, W2, s));
+        }
+        // Rayleigh-Ritz in two stages (FP64).  (1) With Q^2, the operator the filter acts on:
+        // orders the block by Ritz values of Q^2 and gives the damping bound a.  Ordering by Q
+        // instead would pick up mixtures of +lambda and -lambda eigenvectors (same Q^2, so the
+        // filter never separates them) whose Q Rayleigh quotient is near zero.  (2) With Q
+        // inside the first n_ev columns: resolves the signs; ordered by |theta|.
+        Epilogue eq;
+        eq.c_op = 1.0 / h;
+        launch_dslash<double>(c->g, c->p.m0, c->U64, W, QW, m, d_phase, eq, s);
+        CKL();
+        c->dslash_count += m;
+        {
+            std::vector<HostCplx> G2, Y;
+            std::vector<double> mu;
+            TRY(gram_host(c, QW, m, QW, m, G2, s));
+            hermitize(G2, m);
+            host_eigh(m, G2, mu, Y);
+            a = std::min(mu[m - 1], 0.95);
+            TRY(rotate(c, W, m, Y, m, W2, s));
+            TRY(rotate(c, QW, m, Y, m, QW2, s));
+            std::swap(W, W2);
+            std::swap(QW, QW2);
+        }
+        std::vector<HostCplx> T, Z;
+        TRY(gram_host(c, W, n_ev, QW, n_ev, T, s));
+        hermitize(T, n_ev);
+        std::vector<double> w;
+        host_eigh(n_ev, T, w, Z);
+        std::vector<int> order(n_ev);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+            return std::fabs(w[i]) < std::fabs(w[j]) || (std::fabs(w[i]) == std::fabs(w[j]) && w[i] < w[j]);
+        });
+        std::vector<HostCplx> Zs((size_t)n_ev * n_ev);
+        for (int j = 0; j < n_ev; ++j) {
+            theta[j] = w[order[j]];
+            for (int i = 0; i < n_ev; ++i) Zs[i + (size_t)j * n_ev] = Z[i + (size_t)order[j] * n_ev];
+        }
+        // rotate the first n_ev columns in place (through W2/QW2): the block's span is unchanged
+        TRY(rotate(c, W, n_ev, Zs, n_ev, W2, s));
+        TRY(rotate(c, QW, n_ev, Zs, n_ev, QW2, s));
+        CK(cudaMemcpyAsync(W, W2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(QW, QW2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+        // residuals r_i = Q w_i - theta_i w_i, i < n_ev
+        std::vector<double> mth(n_ev), ones(n_ev, 1.0);
+        for (int i = 0; i < n_ev; ++i) mth[i] = -theta[i];
+        CK(cudaMemcpyAsync(tt, QW, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+        launch_axpby<double>(mth.data(), W, ones.data(), tt, n12, n_ev, s);
+        CKL();
+        TRY(ensure_small(c, 0, (long long)kRedBlocks * m, m));
+        norm2_rhs<double>(tt, n12, n_ev, res.data(), c->d_partial, c->d_red, s);
+        worst = 0.0;
+        for (int i = 0; i < n_ev; ++i) worst = std::max(worst, std::sqrt(res[i]));
+        char buf[64];
+        snprintf(buf, sizeof(buf), "%s%.1e", it ? " " : "", worst);
+        hist += buf;
+        if (worst <= tol) {
+            status = OV_OK;
+            break;
+        }
+    }
+    for (int i = 0; i < n_ev; ++i) lambda_out[i] = theta[i];
+    if (V_out) {
+        launch_unpack_spinor<double>(W, V_out, OV_C128, c->g.V, n_ev, s);
+        CKL();
+    }
+    if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
+    CK(cudaStreamSynchronize(s));
+    if (status != OV_OK)
+        return fail(c, status, "eigensolver: not converged after %d filter cycles; worst residual per cycle: %s",
+                    max_iter, hist.c_str());
+    return OV_OK;
+}
+
+}  // extern "C"
+
+// ---- solver ----------------------------------------------------------------------
+
+namespace {
+
+// CG on the chiral-sector normal operator A_s = P_s [2 (1 - m^2/4)(1 + s sign) + m^2] P_s for each
+// system (rhs vector B_k in sector chi_k), in precision R.  Y: solutions.
+template <typename R>
+int inner_cg(ov_ctx* c, double mass, const SysSet& S, const void* B, void* Y, const std::vector<double>& tol_rel,
+             int max_iter, int* iters, cudaStream_t s) {
+    const int prec = prec_of<R>();
+    const int ns = S.n;
+    const long long n12 = 12LL * c->g.V;
+    void *r, *p, *Ap;
+    TRY(workspace(c, "cg_r", prec, ns, &r));
+    TRY(workspace(c, "cg_p", prec, ns, &p));
+    TRY(workspace(c, "cg_Ap", prec, ns, &Ap));
+    const size_t bytes = vec_bytes(c, prec) * ns;
+    CK(cudaMemcpyAsync(r, B, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p, B, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(Y, 0, bytes, s));
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * ns, ns));
+    std::vector<double> rr(ns), rr_new(ns), b2(ns), alpha(ns), beta(ns), ones(ns, 1.0);
+    std::vector<double2> pap(ns);
+    norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
+    b2 = rr;
+    std::vector<char> active(ns);
+    for (int k = 0; k < ns; ++k) active[k] = rr[k] > 0.0;
+    const double k1 = 2.0 * (1.0 - 0.25 * mass * mass);
+    Epilogue fin;
+    fin.c_op = k1 / c->hw_norm;
+    fin.c1 = k1;
+    fin.chi = c->d_chi;
+    fin.c2 = k1 + mass * mass;
+    fin.v2 = p;
+    int it = 0;
+    for (it = 0; it < max_iter; ++it) {
+        bool any = false;
+        for (int k = 0; k < ns; ++k) any = any || active[k];
+        if (!any) break;
+        TRY(sign_pipeline<R>(c, p, S, false, fin, Ap, s));
+        dot_rhs<R>(p, Ap, n12, ns, pap.data(), c->d_partial, c->d_red, s);
+        for (int k = 0; k < ns; ++k) {
+            if (!active[k]) {
+                alpha[k] = 0.0;
+                continue;
+            }
+            if (!std::isfinite(pap[k].x) || !std::isfinite(rr[k]))
+                return fail(c, OV_ERR_NAN, "inner CG: NaN/Inf in <p, A p> (system %d, iteration %d)", k, it);
+            if (pap[k].x <= 0.0)
+                return fail(c, OV_ERR_BREAKDOWN, "inner CG: <p, A p> = %g <= 0 (system %d, iteration %d)", pap[k].x,
+                            k, it);
+            alpha[k] = rr[k] / pap[k].x;
+        }
+        launch_cg_xr<R>(alpha.data(), p, Ap, Y, r, n12, ns, s);
+        CKL();
+        norm2_rhs<R>(r, n12, ns, rr_new.data(), c->d_partial, c->d_red, s);
+        for (int k = 0; k < ns; ++k) {
+            if (!active[k]) {
+                beta[k] = 0.0;
+                continue;
+            }
+            if (std::sqrt(rr_new[k]) <= tol_rel[k] * std::sqrt(b2[k])) active[k] = 0;
+            beta[k] = rr_new[k] / rr[k];
+            rr[k] = rr_new[k];
+        }
+        launch_axpby<R>(ones.data(), r, beta.data(), p, n12, ns, s);  // p = r + beta p
+        CKL();
+    }
+    *iters = it;
+    for (int k = 0; k < ns; ++k)
+        if (active[k]) return OV_ERR_NOT_CONVERGED;
+    return OV_OK;
+}
+
+template <typename R>
+int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* x, double tol, ov_solve_stats* st,
+               cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nrhs = Srhs.n;
+    const int V = c->g.V;
+    const long long n12 = 12LL * V;
+    const int prec = prec_of<R>();
+    const size_t vb64 = vec_bytes(c, OV_PREC_F64);
+    void *B, *X, *Rr, *DX, *S64, *Bs, *Ys, *Ysum, *E, *E64;
+    TRY(workspace(c, "sol_B", OV_PREC_F64, nrhs, &B));
+    TRY(workspace(c, "sol_X", OV_PREC_F64, nrhs, &X));
+    TRY(workspace(c, "sol_R", OV_PREC_F64, nrhs, &Rr));
+    TRY(workspace(c, "sol_DX", OV_PREC_F64, nrhs, &DX));
+    TRY(workspace(c, "sol_S64", OV_PREC_F64, 2 * nrhs, &S64));
+    TRY(workspace(c, "sol_Bs", prec, 2 * nrhs, &Bs));
+    TRY(workspace(c, "sol_Ys", prec, 2 * nrhs, &Ys));
+    TRY(workspace(c, "sol_Ysum", prec, nrhs, &Ysum));
+    TRY(workspace(c, "sol_E", prec, nrhs, &E));
+    TRY(workspace(c, "sol_E64", OV_PREC_F64, nrhs, &E64));
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * 2 * nrhs, 2 * nrhs));
+    launch_pack_spinor<double>(b, OV_C128, B, V, nrhs, s);
+    launch_pack_spinor<double>(x, OV_C128, X, V, nrhs, s);
+    CKL();
+    const long long dslash0 = c->dslash_count, sign0 = c->sign_count;
+    std::vector<double> bn2(nrhs), xn2(nrhs), rn2(nrhs), res(nrhs, 0.0);
+    norm2_rhs<double>(B, n12, nrhs, bn2.data(), c->d_partial, c->d_red, s);
+    norm2_rhs<double>(X, n12, nrhs, xn2.data(), c->d_partial, c->d_red, s);
+    for (int j = 0; j < nrhs; ++j)
+        if (!std::isfinite(bn2[j]) || !std::isfinite(xn2[j])) return fail(c, OV_ERR_NAN, "NaN/Inf in b or x (rhs %d)", j);
+    std::vector<double> ones(nrhs, 1.0), mones(nrhs, -1.0);
+    auto true_residual = [&]() -> int {
+        TRY(overlap_op<double>(c, X, Srhs, mass, false, DX, s));
+        CK(cudaMemcpyAsync(Rr, B, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        launch_axpby<double>(mones.data(), DX, ones.data(), Rr, n12, nrhs, s);  // R = B - D X
+        CKL();
+        norm2_rhs<double>(Rr, n12, nrhs, rn2.data(), c->d_partial, c->d_red, s);
+        for (int j = 0; j < nrhs; ++j) {
+            if (!std::isfinite(rn2[j])) return fail(c, OV_ERR_NAN, "NaN/Inf in the true residual (rhs %d)", j);
+            res[j] = bn2[j] > 0.0 ? std::sqrt(rn2[j] / bn2[j]) : 0.0;
+        }
+        return OV_OK;
+    };
+    bool xzero = true;
+    for (int j = 0; j < nrhs; ++j) xzero = xzero && xn2[j] == 0.0;
+    if (xzero) {
+        CK(cudaMemcpyAsync(Rr, B, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        for (int j = 0; j < nrhs; ++j) res[j] = bn2[j] > 0.0 ? 1.0 : 0.0;
+        rn2 = bn2;
+    } else {
+        TRY(true_residual());
+    }
+    const double base_tol = c->p.inner_tol > 0.0 ? c->p.inner_tol : (prec == OV_PREC_F64 ? 0.0 : 1e-5);
+    int outer = 0, inner_total = 0, status = OV_OK;
+    const int max_outer = 60;
+    while (true) {
+        double worst = 0.0;
+        for (int j = 0; j < nrhs; ++j) worst = std::max(worst, res[j]);
+        if (worst <= tol) break;
+        if (outer >= max_outer || inner_total >= c->p.max_iter) {
+            status = OV_ERR_NOT_CONVERGED;
+            break;
+        }
+        // chiral sectors of the residuals of the unconverged right-hand sides
+        std::vector<int> src, sys_of_rhs(2 * nrhs, -1);
+        std::vector<signed char> chi;
+        for (int j = 0; j < nrhs; ++j)
+            if (res[j] > tol)
+                for (int sg = 0; sg < 2; ++sg) {
+                    src.push_back(j);
+                    chi.push_back(sg == 0 ? 1 : -1);
+                }
+        const int ns0 = (int)src.size();
+        CK(cudaMemcpyAsync(c->d_idx, src.data(), sizeof(int) * ns0, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->d_chi, chi.data(), ns0, cudaMemcpyHostToDevice, s));
+        launch_chiral_split<double>(Rr, S64, c->d_idx, c->d_chi, V, ns0, s);
+        CKL();
+        std::vector<double> sn2(ns0);
+        norm2_rhs<double>(S64, n12, ns0, sn2.data(), c->d_partial, c->d_red, s);
+        // keep the non-zero sectors, compacted
+        SysSet S;
+        std::vector<double> tol_rel;
+        int ns = 0;
+        for (int k = 0; k < ns0; ++k) {
+            const int j = src[k];
+            if (!(sn2[k] > 0.0)) continue;
+            if (ns != k)
+                CK(cudaMemcpyAsync((char*)S64 + (size_t)ns * vb64, (char*)S64 + (size_t)k * vb64, vb64,
+                                   cudaMemcpyDeviceToDevice, s));
+            S.phase.push_back(Srhs.phase[j]);
+            S.chi.push_back(chi[k]);
+            sys_of_rhs[2 * j + (chi[k] > 0 ? 0 : 1)] = ns;
+            const double want = 0.5 * tol * std::sqrt(bn2[j] / sn2[k]);
+            tol_rel.push_back(std::min(0.5, std::max(base_tol, want)));
+            ++ns;
+        }
+        S.n = ns;
+        if (std::is_same<R, double>::value)
+            CK(cudaMemcpyAsync(Bs, S64, vb64 * ns, cudaMemcpyDeviceToDevice, s));
+        else
+            launch_convert<double, R>(S64, Bs, n12 * ns, s);
+        CKL();
+        int iters = 0;
+        int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s);
+        inner_total += iters;
+        if (rc != OV_OK && rc != OV_ERR_NOT_CONVERGED) {
+            status = rc;
+            break;
+        }
+        // y_j = y_{j,+} + y_{j,-};  e_j = D(m)^+ y_j;  x_j += e_j
+        CK(cudaMemcpyAsync(c->d_idx, sys_of_rhs.data(), sizeof(int) * 2 * nrhs, cudaMemcpyHostToDevice, s));
+        {
+            dim3 grid(std::min<long long>((n12 + 255) / 256, 152 * 4), nrhs);
+            merge_sectors_k<R><<<grid, 256, 0, s>>>((const typename C2<R>::T*)Ys, c->d_idx,
+                                                    (typename C2<R>::T*)Ysum, n12);
+            count_launch();
+            CKL();
+        }
+        TRY(overlap_op<R>(c, Ysum, Srhs, mass, true, E, s));
+        if (std::is_same<R, double>::value)
+            CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        else
+            launch_convert<R, double>(E, E64, n12 * nrhs, s);
+        launch_axpby<double>(ones.data(), E64, ones.data(), X, n12, nrhs, s);
+        CKL();
+        ++outer;
+        TRY(true_residual());
+    }
+    launch_unpack_spinor<double>(X, x, OV_C128, V, nrhs, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    if (st) {
+        st->status = status;
+        st->outer_iters = outer;
+        st->inner_iters = inner_total;
+        st->sign_applies = c->sign_count - sign0;
+        st->dslash_calls = c->dslash_count - dslash0;
+        double worst = 0.0;
+        for (int j = 0; j < nrhs; ++j) worst = std::max(worst, res[j]);
+        st->true_residual = worst;
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status != OV_OK) {
+        if (c->err.empty() || status == OV_ERR_NOT_CONVERGED)
+            fail(c, status, "solve_overlap: status %d after %d outer / %d inner iterations", status, outer, inner_total);
+        return status;
+    }
+    return OV_OK;
+}
+
+}  // namespace
+
+extern "C" int solve_overlap(ov_ctx* c, double mass, const double* phase, const void* b, void* x, int nrhs, double tol,
+                             ov_solve_stats* stats, ov_stream_t stream) {
+    TRY(check_ready(c, b, x, nrhs));
+    if (!(tol > 0.0) || !std::isfinite(mass)) return fail(c, OV_ERR_ARG, "tol must be > 0 and mass finite");
+    SysSet S = make_sys(nrhs, phase);
+    TRY(phase_check(c, S));
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->p.inner_precision == OV_PREC_F64 ? solve_impl<double>(c, mass, S, b, x, tol, stats, s)
+                                               : solve_impl<float>(c, mass, S, b, x, tol, stats, s);
+}

@@ -1,0 +1,142 @@
+// Small dense linear algebra on the host, for the m x m matrices of the
+// small-space setup (Gram matrices for Cholesky-QR re-orthonormalisation and
+// the Rayleigh-Ritz matrices of the eigensolver), and the Chebyshev
+// coefficients of the polynomial P(x) ~ x^{-1/2} (Sec. 2).
+//
+// Matrices are column-major arrays of (re, im) pairs, A(i, j) = A[i + j n].
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <numeric>
+#include <vector>
+
+#include "ovl_internal.h"
+
+namespace ovl {
+namespace {
+typedef std::complex<double> cd;
+inline cd get(const std::vector<HostCplx>& A, int n, int i, int j) {
+    const HostCplx& v = A[i + (size_t)j * n];
+    return cd(v.re, v.im);
+}
+inline void put(std::vector<HostCplx>& A, int n, int i, int j, cd v) {
+    A[i + (size_t)j * n] = HostCplx{v.real(), v.imag()};
+}
+}  // namespace
+
+bool host_cholesky(int n, std::vector<HostCplx>& A) {
+    for (int j = 0; j < n; ++j) {
+        double d = get(A, n, j, j).real();
+        for (int k = 0; k < j; ++k) d -= std::norm(get(A, n, j, k));
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        const double ljj = std::sqrt(d);
+        put(A, n, j, j, cd(ljj, 0.0));
+        for (int i = j + 1; i < n; ++i) {
+            cd s = get(A, n, i, j);
+            for (int k = 0; k < j; ++k) s -= get(A, n, i, k) * std::conj(get(A, n, j, k));
+            put(A, n, i, j, s / ljj);
+        }
+        for (int i = 0; i < j; ++i) put(A, n, i, j, cd(0.0, 0.0));  // clear the upper triangle
+    }
+    return true;
+}
+
+void host_inv_lower_dag(int n, const std::vector<HostCplx>& L, std::vector<HostCplx>& R) {
+    // X = L^{-1} (lower) by forward substitution, column by column; R = X^+.
+    std::vector<cd> X((size_t)n * n, cd(0.0, 0.0));
+    for (int c = 0; c < n; ++c) {
+        for (int i = c; i < n; ++i) {
+            cd s = (i == c) ? cd(1.0, 0.0) : cd(0.0, 0.0);
+            for (int k = c; k < i; ++k) s -= get(L, n, i, k) * X[k + (size_t)c * n];
+            X[i + (size_t)c * n] = s / get(L, n, i, i);
+        }
+    }
+    R.assign((size_t)n * n, HostCplx{0.0, 0.0});
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) put(R, n, i, j, std::conj(X[j + (size_t)i * n]));
+}
+
+void host_eigh(int n, std::vector<HostCplx>& Ain, std::vector<double>& w, std::vector<HostCplx>& Zout) {
+    // Cyclic Jacobi for a Hermitian matrix.  Each rotation J acts on columns p, q:
+    // with a_pq = r e^{i phi}, D = diag(1, e^{-i phi}) makes the (p, q) block real,
+    // and the real rotation [[c, s], [-s, c]] with tan(2 theta) = 2 r / (a_qq - a_pp)
+    // zeroes it; A <- J^+ A J and Z <- Z J.
+    std::vector<cd> A((size_t)n * n), Z((size_t)n * n, cd(0.0, 0.0));
+    for (size_t k = 0; k < A.size(); ++k) A[k] = cd(Ain[k].re, Ain[k].im);
+    for (int i = 0; i < n; ++i) Z[i + (size_t)i * n] = 1.0;
+    auto at = [&](int i, int j) -> cd& { return A[i + (size_t)j * n]; };
+    double fro = 0.0;
+    for (auto& v : A) fro += std::norm(v);
+    fro = std::sqrt(fro);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+                if (i != j) off += std::norm(at(i, j));
+        if (std::sqrt(off) <= 1e-15 * fro || fro == 0.0) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                const cd apq = at(p, q);
+                const double r = std::abs(apq);
+                if (r <= 1e-300) continue;
+                const cd e = apq / r;  // e^{i phi}
+                const double app = at(p, p).real(), aqq = at(q, q).real();
+                const double theta = 0.5 * std::atan2(2.0 * r, aqq - app);
+                const double c = std::cos(theta), s = std::sin(theta);
+                const cd em = std::conj(e);  // e^{-i phi}
+                // columns: col_p' = c col_p - s e^{-i phi} col_q ; col_q' = s col_p + c e^{-i phi} col_q
+                for (int k = 0; k < n; ++k) {
+                    const cd akp = at(k, p), akq = at(k, q);
+                    at(k, p) = c * akp - s * em * akq;
+                    at(k, q) = s * akp + c * em * akq;
+                    const cd zkp = Z[k + (size_t)p * n], zkq = Z[k + (size_t)q * n];
+                    Z[k + (size_t)p * n] = c * zkp - s * em * zkq;
+                    Z[k + (size_t)q * n] = s * zkp + c * em * zkq;
+                }
+                // rows: row_p' = c row_p - s e^{i phi} row_q ; row_q' = s row_p + c e^{i phi} row_q
+                for (int k = 0; k < n; ++k) {
+                    const cd apk = at(p, k), aqk = at(q, k);
+                    at(p, k) = c * apk - s * e * aqk;
+                    at(q, k) = s * apk + c * e * aqk;
+                }
+                at(p, q) = 0.0;
+                at(q, p) = 0.0;
+                at(p, p) = cd(at(p, p).real(), 0.0);
+                at(q, q) = cd(at(q, q).real(), 0.0);
+            }
+        }
+    }
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return at(a, a).real() < at(b, b).real(); });
+    w.resize(n);
+    Zout.assign((size_t)n * n, HostCplx{0.0, 0.0});
+    for (int j = 0; j < n; ++j) {
+        w[j] = at(order[j], order[j]).real();
+        for (int i = 0; i < n; ++i) {
+            const cd v = Z[i + (size_t)order[j] * n];
+            Zout[i + (size_t)j * n] = HostCplx{v.real(), v.imag()};
+        }
+    }
+    for (size_t k = 0; k < A.size(); ++k) Ain[k] = HostCplx{A[k].real(), A[k].imag()};
+}
+
+void host_chebyshev_coeffs(int n, double eps, double* out) {
+    // Interpolation at the Chebyshev-Gauss nodes y_j = cos(theta_j), theta_j = pi (j + 1/2)/(n + 1),
+    // mapped to x_j = ((1 - eps) y_j + 1 + eps)/2 in [eps, 1]; f(x) = x^{-1/2}.
+    const double pi = std::acos(-1.0);
+    std::vector<double> f(n + 1), th(n + 1);
+    for (int j = 0; j <= n; ++j) {
+        th[j] = pi * (j + 0.5) / (n + 1);
+        const double x = ((1.0 - eps) * std::cos(th[j]) + 1.0 + eps) / 2.0;
+        f[j] = 1.0 / std::sqrt(x);
+    }
+    for (int k = 0; k <= n; ++k) {
+        double s = 0.0;
+        for (int j = 0; j <= n; ++j) s += f[j] * std::cos(k * th[j]);
+        out[k] = 2.0 * s / (n + 1);
+    }
+    out[0] *= 0.5;
+}
+
+}  // namespace ovl

@@ -1,0 +1,124 @@
+// Internal declarations of libovl: data layouts, kernel launchers, host helpers.
+//
+// Internal layouts (all site-major over the fastest index so that a warp reads
+// 32 consecutive sites of one component):
+//   spinor  [rhs][12][V]    complex<R>, component k = 3*spin + colour
+//   links   [4][9][V]       complex<R>, entry 3*a + b of U_mu(n)
+//   bank    [n_ev][12][V]   complex<R> (the same layout as a spinor)
+// with R = double (OV_PREC_F64) or float (OV_PREC_F32).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ovl {
+
+// Number of kernels this library has launched (all contexts, all streams).
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+template <typename R> struct C2;
+template <> struct C2<double> { typedef double2 T; };
+template <> struct C2<float> { typedef float2 T; };
+
+// Lattice geometry and boundary factors (1 periodic, -1 antiperiodic, 0 Dirichlet).
+struct Geom {
+    int L[4];       // Lx, Ly, Lz, Lt
+    int V;          // sites
+    double bcf[4];  // boundary factor per direction
+};
+
+// Epilogue of a Wilson application (all coefficients uniform over right-hand sides):
+//   z   = c_op * H_w(in) + c1 * v1
+//   z   = gamma5 z                          if g5
+//   z   = chi_j * P_{chi_j} z               if chi && chi[j] != 0  (P_+- = (1 +- gamma5)/2)
+//   out = z + c2 * v2 + c3 * v3
+// Null vectors contribute nothing.  v3 may alias out (read and written by the same thread).
+struct Epilogue {
+    double c_op = 1.0;
+    double c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    const void* v1 = nullptr;
+    const void* v2 = nullptr;
+    const void* v3 = nullptr;
+    int g5 = 0;
+    const signed char* chi = nullptr;  // device [nrhs]
+};
+
+// ---- kernels: dslash.cu ---------------------------------------------------
+template <typename R>
+void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
+                   const double* d_phase, const Epilogue& e, cudaStream_t s);
+
+// ---- kernels: blas.cu -----------------------------------------------------
+// ABI spinor [rhs][site][12] (dtype_in: 0 complex128, 1 complex64) -> internal [rhs][12][V] of R.
+template <typename R>
+void launch_pack_spinor(const void* abi, int dtype_in, void* internal, int V, int nrhs, cudaStream_t s);
+template <typename R>
+void launch_unpack_spinor(const void* internal, void* abi, int dtype_out, int V, int nrhs, cudaStream_t s);
+// ABI links [4][site][3][3] -> internal [4][9][V] of R.
+template <typename R>
+void launch_pack_gauge(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s);
+// Element-wise conversion between precisions (same layout), n complex numbers.
+template <typename RI, typename RO>
+void launch_convert(const void* in, void* out, long long n, cudaStream_t s);
+
+// Per-rhs reductions over n complex numbers each (vectors at stride n).  Results are
+// written to host memory after an internal synchronisation of s.  Deterministic.
+template <typename R>
+void dot_rhs(const void* a, const void* b, long long n, int nrhs, double2* host_out, double2* d_partial,
+             double2* d_out, cudaStream_t s);
+template <typename R>
+void norm2_rhs(const void* a, long long n, int nrhs, double* host_out, double2* d_partial, double2* d_out,
+               cudaStream_t s);
+
+// y_j = a_j x_j + b_j y_j for per-rhs real scalars (host arrays of length nrhs <= kMaxRhs).
+constexpr int kMaxRhs = 256;
+template <typename R>
+void launch_axpby(const double* a, const void* x, const double* b, void* y, long long n, int nrhs, cudaStream_t s);
+// CG step: x_j += alpha_j p_j; r_j -= alpha_j Ap_j.
+template <typename R>
+void launch_cg_xr(const double* alpha, const void* p, const void* Ap, void* x, void* r, long long n, int nrhs,
+                  cudaStream_t s);
+// Scale by a complex scalar per rhs is not needed; plain scale by a uniform real:
+template <typename R>
+void launch_scale(double a, const void* x, void* y, long long n, cudaStream_t s);
+// y = P_chi x per rhs (chi in {+1,-1}; spins 0,1 for +1, 2,3 for -1), V sites, rhs mapping
+// out rhs j <- in rhs src[j].
+template <typename R>
+void launch_chiral_split(const void* x, void* y, const int* src, const signed char* chi, int V, int nsys,
+                         cudaStream_t s);
+// y = gamma5 x.
+template <typename R>
+void launch_gamma5(const void* x, void* y, int V, int nrhs, cudaStream_t s);
+
+// C[i][j] = <A_i, B_j> over n complex numbers; A_i at A + i*strideA, B_j at B + j*strideB
+// (strides in complex elements).  C: device double2 [na][nb] (row-major), deterministic.
+template <typename R>
+void multidot(const void* A, long long strideA, int na, const void* B, long long strideB, int nb, long long n,
+              double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s);
+// out_j = alpha * X_j + sum_i A_i C[i][j] for j < nb; C is device double2 [na][ldc] (column j).
+template <typename R>
+void combine(const void* A, long long strideA, int na, const double2* d_C, int ldc, int nb, double alpha,
+             const void* X, long long strideX, void* out, long long strideO, long long n, cudaStream_t s);
+
+// Partial-sum buffer size (double2 elements) needed by dot_rhs/norm2_rhs.
+constexpr int kRedBlocks = 608;
+
+// ---- host linear algebra: hostla.cpp --------------------------------------
+// Column-major complex matrices as std::vector<double2>-compatible arrays of (re, im).
+struct HostCplx { double re, im; };
+// Cholesky A = L L^+ (lower); returns false if not positive definite.
+bool host_cholesky(int n, std::vector<HostCplx>& A);
+// Inverse of the conjugate transpose of a lower-triangular L: returns R = L^{-+} (upper).
+void host_inv_lower_dag(int n, const std::vector<HostCplx>& L, std::vector<HostCplx>& R);
+// Eigen-decomposition of a Hermitian matrix (cyclic Jacobi): A = Z diag(w) Z^+,
+// eigenvalues ascending. A is overwritten.
+void host_eigh(int n, std::vector<HostCplx>& A, std::vector<double>& w, std::vector<HostCplx>& Z);
+// Chebyshev interpolant coefficients of x^{-1/2} on [eps, 1] (c_0 halved).
+void host_chebyshev_coeffs(int n, double eps, double* out);
+
+}  // namespace ovl

@@ -1,0 +1,282 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+FP64 results must agree with the oracle to 1e-12 relative per operator
+application (max |difference| / max |oracle|).  FP32 results are held to a
+bound derived from single-precision rounding (see ``F32_TOL``).  Lattices
+span several 128-site thread blocks with ragged tails, plus the 2^4 case in
+which forward and backward neighbours coincide.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, dirac
+from oracle import overlap as ov
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+# One Wilson application sums 9 terms of O(1) per component in FP32: a few ulps (6e-8) each.
+F32_WILSON_TOL = 2e-6
+M0 = -1.5
+
+
+def relerr(got, want):
+    return float(np.abs(got - want).max() / np.abs(want).max())
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1111_6288_gb300 as P
+
+    return P
+
+
+def to_dev(a, dtype=None):
+    import torch
+
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def make_ctx(P, dims, bc=(0, 0, 0, 1), precision=0, inner=0, eps=0.01, degree=30, hw_norm=0.0, max_nrhs=8,
+             inner_tol=0.0):
+    return P.Context(P.Params(dims=dims, bc=bc, m0=M0, hw_norm=hw_norm, eps=eps, poly_degree=degree,
+                              precision=precision, inner_precision=inner, max_nrhs=max_nrhs, inner_tol=inner_tol))
+
+
+BC_NUM = {0: 1.0, 1: -1.0, 2: 0.0}
+
+
+def oracle_bc(bc):
+    return tuple(BC_NUM[b] for b in bc)
+
+
+def gpu_apply(P, ctx, fn, x, **kw):
+    import torch
+
+    xd = to_dev(x, ctx.spinor_dtype())
+    out = torch.empty_like(xd)
+    fn(ctx, xd, out, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# Wilson operator
+# ---------------------------------------------------------------------------
+
+WILSON_CASES = [
+    ((2, 2, 2, 2), (0, 0, 0, 1), [0.0]),
+    ((4, 4, 4, 4), (0, 0, 0, 1), [0.0, 0.3]),
+    ((6, 4, 3, 6), (2, 0, 0, 2), [0.4, -0.2, 0.0]),  # 432 sites: 3 blocks + a ragged tail
+    ((5, 3, 4, 7), (1, 2, 0, 0), [1.3]),
+]
+
+
+@pytest.mark.parametrize("dims,bc,phases", WILSON_CASES)
+@pytest.mark.parametrize("hermitian", [False, True])
+def test_wilson_f64_matches_oracle(P, dims, bc, phases, hermitian):
+    U = synth.random_su3_field(dims, 0.4, 11)
+    x = synth.gaussian_spinor(dims, len(phases), 12)
+    ctx = make_ctx(P, dims, bc)
+    ctx.set_gauge(to_dev(U))
+    got = gpu_apply(P, ctx, P.apply_wilson, x, phase=phases, hermitian=hermitian)
+    f = dirac.hermitian_wilson if hermitian else dirac.wilson
+    want = np.stack([f(U, x[j], M0, oracle_bc(bc), phases[j]) for j in range(len(phases))])
+    assert relerr(got, want) < F64_TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,bc,phases", WILSON_CASES[1:3])
+def test_wilson_f32_matches_oracle(P, dims, bc, phases):
+    U = synth.random_su3_field(dims, 0.4, 11)
+    x = synth.gaussian_spinor(dims, len(phases), 12)
+    ctx = make_ctx(P, dims, bc, precision=1)
+    ctx.set_gauge(to_dev(U))
+    got = gpu_apply(P, ctx, P.apply_wilson, x, phase=phases, hermitian=True)
+    want = np.stack([dirac.hermitian_wilson(U, x[j], M0, oracle_bc(bc), phases[j]) for j in range(len(phases))])
+    assert relerr(got, want) < F32_WILSON_TOL
+    ctx.close()
+
+
+def test_wilson_batched_equals_one_by_one(P):
+    import torch
+
+    dims = (4, 4, 4, 6)
+    U = synth.random_su3_field(dims, 0.3, 2)
+    x = synth.gaussian_spinor(dims, 4, 3)
+    ctx = make_ctx(P, dims)
+    ctx.set_gauge(to_dev(U))
+    phases = [0.0, 0.1, -0.3, 0.0]
+    batched = gpu_apply(P, ctx, P.apply_wilson, x, phase=phases, hermitian=True)
+    for j in range(4):
+        one = gpu_apply(P, ctx, P.apply_wilson, x[j:j + 1], phase=[phases[j]], hermitian=True)
+        assert np.array_equal(one[0], batched[j])
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# sign function and overlap with an exact small space (4^4, degree 200)
+# ---------------------------------------------------------------------------
+
+# Q^2 interval for the 4^4 field below: its smallest |Q| is 0.050 (0.059 after removing 8
+# modes), so [0.002, 1] holds the whole large-space spectrum and the Chebyshev recurrence
+# stays inside [-1, 1].  (An interval that misses part of the spectrum evaluates T_k outside
+# [-1, 1], where the recurrence amplifies rounding by cosh(k acosh|y|) and no two
+# implementations agree to 1e-12.)
+EPS4 = 0.002
+
+
+@pytest.fixture(scope="module")
+def lat4():
+    """4^4, links eps = 0.3, seed 0: exact 8 lowest |lambda| eigenvectors of Q (dense)."""
+    dims = (4, 4, 4, 4)
+    bc = (0, 0, 0, 1)
+    U = synth.random_su3_field(dims, 0.3, 0)
+    hw = 6.5  # the bound |4 + m0| + 4 the library uses by default
+    H = dense.hw_matrix(U, M0, oracle_bc(bc))
+    lam, W, lam_all, W_all = dense.low_modes(H, hw, 8)
+    V = dense.vectors_to_fields(W, synth.site_shape(dims))
+    assert np.sort(np.abs(lam_all))[0] ** 2 > EPS4
+    return dict(dims=dims, bc=bc, U=U, hw=hw, lam=lam, V=V, lam_all=lam_all)
+
+
+def oracle_params(d, degree, eps):
+    return ov.OverlapParams(m0=M0, hw_norm=d["hw"], eps=eps, degree=degree, bc=oracle_bc(d["bc"]))
+
+
+@pytest.mark.parametrize("n_ev", [0, 8])
+def test_sign_f64_matches_oracle(P, lat4, n_ev):
+    d = lat4
+    degree, eps = 200, EPS4
+    ctx = make_ctx(P, d["dims"], d["bc"], degree=degree, eps=eps)
+    ctx.set_gauge(to_dev(d["U"]))
+    small = ov.SmallSpace.empty(synth.site_shape(d["dims"]))
+    if n_ev:
+        P.deflate(ctx, to_dev(d["V"][:n_ev]), d["lam"][:n_ev])
+        small = ov.SmallSpace.from_eigenpairs(d["V"][:n_ev], d["lam"][:n_ev])
+    x = synth.gaussian_spinor(d["dims"], 2, 5)
+    got = gpu_apply(P, ctx, P.apply_sign_Hw, x)
+    p = oracle_params(d, degree, eps)
+    want = np.stack([ov.sign_hw(d["U"], x[j], p, small) for j in range(2)])
+    assert relerr(got, want) < F64_TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("mass", [0.0, 0.1])
+def test_overlap_f64_matches_oracle(P, lat4, mass):
+    d = lat4
+    degree, eps = 200, EPS4
+    ctx = make_ctx(P, d["dims"], d["bc"], degree=degree, eps=eps)
+    ctx.set_gauge(to_dev(d["U"]))
+    P.deflate(ctx, to_dev(d["V"]), d["lam"])
+    small = ov.SmallSpace.from_eigenpairs(d["V"], d["lam"])
+    x = synth.gaussian_spinor(d["dims"], 1, 1)
+    got = gpu_apply(P, ctx, P.apply_overlap, x, mass=mass)
+    want = ov.overlap(d["U"], x[0], mass, oracle_params(d, degree, eps), small)
+    assert relerr(got[0], want) < F64_TOL
+    ctx.close()
+
+
+def test_overlap_ragged_lattice_field_phases_random_banks(P):
+    """6x4x3x6 (ragged), Dirichlet x and t, three right-hand sides at two field
+    phases with a different (random orthonormal) small space for each phase."""
+    dims, bc = (6, 4, 3, 6), (2, 0, 0, 2)
+    U = synth.random_su3_field(dims, 0.3, 21)
+    site = synth.site_shape(dims)
+    rng = np.random.default_rng(22)
+    banks = {}
+    degree, eps, mass = 24, 0.02, 0.05
+    ctx = make_ctx(P, dims, bc, degree=degree, eps=eps)
+    ctx.set_gauge(to_dev(U))
+    for phase, nev in [(0.0, 5), (0.25, 3)]:
+        A = rng.standard_normal((12 * 432, nev)) + 1j * rng.standard_normal((12 * 432, nev))
+        Qm, _ = np.linalg.qr(A)
+        V = dense.vectors_to_fields(Qm, site)
+        lam = rng.standard_normal(nev)
+        banks[phase] = ov.SmallSpace.from_eigenpairs(V, lam)
+        P.deflate(ctx, to_dev(V), lam, phase=phase)
+    phases = [0.25, 0.0, 0.25]
+    x = synth.gaussian_spinor(dims, 3, 23)
+    got = gpu_apply(P, ctx, P.apply_overlap, x, mass=mass, phase=phases)
+    p = ov.OverlapParams(m0=M0, hw_norm=6.5, eps=eps, degree=degree, bc=oracle_bc(bc))
+    for j in range(3):
+        want = ov.overlap(U, x[j], mass, p, banks[phases[j]], phases[j])
+        assert relerr(got[j], want) < F64_TOL
+    ctx.close()
+
+
+def test_sign_f32_error_is_stated(P, lat4):
+    """FP32 sign(H_w) against the FP64 oracle: degree-200 Clenshaw in single precision."""
+    d = lat4
+    ctx = make_ctx(P, d["dims"], d["bc"], degree=200, eps=EPS4, precision=1)
+    ctx.set_gauge(to_dev(d["U"]))
+    P.deflate(ctx, to_dev(d["V"]), d["lam"])
+    x = synth.gaussian_spinor(d["dims"], 1, 5)
+    got = gpu_apply(P, ctx, P.apply_sign_Hw, x)
+    small = ov.SmallSpace.from_eigenpairs(d["V"], d["lam"])
+    want = ov.sign_hw(d["U"], x[0], oracle_params(d, 200, EPS4), small)
+    err = relerr(got[0], want)
+    print(f"FP32 sign(H_w) relative error vs FP64 oracle at n = 200: {err:.3e}")
+    assert err < 1e-4
+    ctx.close()
+
+
+def test_missing_bank_for_nonzero_phase_is_an_error(P, lat4):
+    d = lat4
+    ctx = make_ctx(P, d["dims"], d["bc"])
+    ctx.set_gauge(to_dev(d["U"]))
+    x = to_dev(synth.gaussian_spinor(d["dims"], 1, 5))
+    import torch
+
+    with pytest.raises(P.OvlError) as e:
+        P.apply_sign_Hw(ctx, x, torch.empty_like(x), phase=[0.5])
+    assert e.value.code == 8
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# solver
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("inner", [0, 1])
+def test_solve_reaches_tolerance_and_matches_oracle(P, lat4, inner):
+    import torch
+
+    d = lat4
+    degree, eps, mass, tol = 200, EPS4, 0.1, 1e-10
+    ctx = make_ctx(P, d["dims"], d["bc"], degree=degree, eps=eps, inner=inner)
+    ctx.set_gauge(to_dev(d["U"]))
+    P.deflate(ctx, to_dev(d["V"]), d["lam"])
+    b = synth.point_sources(d["dims"], [(0, 1), (3, 2)])
+    bd = to_dev(b)
+    xd = torch.zeros_like(bd)
+    st = P.solve_overlap(ctx, bd, xd, mass, tol=tol)
+    x = xd.cpu().numpy()
+    assert st.true_residual <= tol
+    small = ov.SmallSpace.from_eigenpairs(d["V"], d["lam"])
+    p = oracle_params(d, degree, eps)
+    for j in range(2):
+        r = b[j] - ov.overlap(d["U"], x[j], mass, p, small)
+        assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol  # oracle's own operator
+    print(f"inner precision {inner}: outer {st.outer_iters}, inner {st.inner_iters}, residual {st.true_residual:.2e}")
+    ctx.close()
+
+
+def test_eigensolver_matches_dense(P, lat4):
+    d = lat4
+    ctx = make_ctx(P, d["dims"], d["bc"])
+    ctx.set_gauge(to_dev(d["U"]))
+    lam, V = P.eigensolve_Q(ctx, 8, tol=1e-11, max_iter=200, want_vectors=True)
+    assert np.allclose(np.sort(lam), np.sort(d["lam"]), atol=1e-10)
+    Vh = V.cpu().numpy()
+    for i in range(8):
+        r = dirac.hermitian_wilson(d["U"], Vh[i], M0, oracle_bc(d["bc"])) / d["hw"] - lam[i] * Vh[i]
+        assert np.linalg.norm(r) < 1e-10
+    ctx.close()

@@ -1,0 +1,96 @@
+"""Host-side checks of libovl that need no GPU: the library builds and loads,
+exports every symbol include/ovl.h declares, validates arguments on the host,
+and its host routines (Chebyshev coefficients, small Hermitian eigensolver)
+agree with independent references."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import chebyshev
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ovl():
+    import paper_1111_6288_gb300 as P
+    from paper_1111_6288_gb300 import build
+
+    if not os.path.exists(P.library_path()):
+        build.build()
+    return P
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\([^;]*\)\s*;", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for want in ["apply_wilson", "apply_sign_Hw", "apply_overlap", "deflate", "solve_overlap", "ov_create",
+                 "ov_destroy", "ov_set_gauge", "ov_eigensolve_Q"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(ovl):
+    L = ctypes.CDLL(ovl.library_path())
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_library_chebyshev_coefficients_match_oracle(ovl):
+    for n, eps in [(13, 0.0036), (200, 0.01), (527, 4e-4), (1054, 1e-4)]:
+        got = ovl.chebyshev_coeffs(n, eps)
+        want = chebyshev.chebyshev_coeffs(n, eps)
+        assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64])
+def test_host_eigh_matches_numpy(ovl, n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = A + A.conj().T
+    A[0, min(1, n - 1)] += 0  # keep Hermitian
+    w, Z = ovl.host_eigh(A)
+    assert np.allclose(w, np.linalg.eigvalsh(A), atol=1e-12 * np.abs(w).max())
+    assert np.allclose(Z.conj().T @ Z, np.eye(n), atol=1e-12)
+    assert np.allclose(A @ Z, Z * w, atol=1e-11 * np.abs(w).max())
+
+
+def test_host_eigh_degenerate(ovl):
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12)))
+    w0 = np.array([1, 1, 1, 2, 2, -3, -3, 0.5, 0.5, 0.5, 0.5, 7.0])
+    A = (Q * w0) @ Q.conj().T
+    w, Z = ovl.host_eigh(A)
+    assert np.allclose(w, np.sort(w0), atol=1e-12)
+    assert np.allclose(A @ Z, Z * w, atol=1e-11)
+
+
+@pytest.mark.parametrize("bad", [dict(dims=(1, 4, 4, 4)), dict(eps=0.0), dict(eps=1.0), dict(poly_degree=0),
+                                 dict(precision=7), dict(max_nrhs=0), dict(bc=(0, 0, 0, 5))])
+def test_create_rejects_invalid_parameters(ovl, bad):
+    kw = dict(dims=(4, 4, 4, 4))
+    kw.update(bad)
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.Context(ovl.Params(**kw))
+    assert e.value.code == 1
+
+
+def test_create_resolves_norm_bound(ovl):
+    ctx = ovl.Context(ovl.Params(dims=(4, 4, 4, 8), m0=-1.5))
+    assert ctx.volume == 512
+    assert ctx.hw_norm == pytest.approx(6.5)
+    ctx.close()
