@@ -211,6 +211,27 @@ def run_reference(args):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+def kernel_case():
+    """A few FP32 Wilson-kernel launches (plain and Clenshaw-epilogue) at 24^3 x 48."""
+    import torch
+
+    import paper_1111_6288_gb300 as P
+    import synth
+
+    dims = (24, 24, 24, 48)
+    U = torch.from_numpy(synth.random_su3_field(dims, LINK_EPS, 0)).cuda()
+    ctx = P.Context(P.Params(dims=dims, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=4, precision=P.OV_PREC_F32,
+                             inner_precision=P.OV_PREC_F32, max_nrhs=1))
+    ctx.set_gauge(U)
+    del U
+    x = torch.from_numpy(synth.gaussian_spinor(dims, 1, 1)).to(torch.complex64).cuda()
+    y = torch.empty_like(x)
+    for _ in range(2):
+        P.apply_overlap(ctx, x, y, mass=MASS)
+    torch.cuda.synchronize()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,12 +240,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the FP64-only comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="profiling case: a few FP32 Wilson-kernel launches on 24^3x48 (links 191 MB > L2), "
+                         "then exit without a JSON line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.kernel_case:
+        kernel_case()
         return
 
     import numpy as np
@@ -283,10 +310,12 @@ def main():
     torch.cuda.synchronize()
     launches0 = P.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     stats = [step(ctx_mix) for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = P.launch_count() - launches0
     barrier(world)
     clk = clocks.stop()
