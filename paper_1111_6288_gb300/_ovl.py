@@ -81,6 +81,7 @@ _SIGNATURES = {
     "apply_wilson": (_I, [_VP, _VP, _VP, _I, _DP, _I, _VP]),
     "apply_sign_Hw": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
     "apply_overlap": (_I, [_VP, _VP, _VP, _I, _D, _DP, _VP]),
+    "apply_wilson_noalloc": (_I, [C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _VP, _VP, _VP, _I, _DP, _I, _VP]),
     "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
     "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
     "solve_overlap": (_I, [_VP, _D, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),

@@ -585,6 +585,8 @@ int cheb_filter(ov_ctx* c, void* W64, int m, double a, int degree, const double*
 
 }  // namespace
 
+void ovl::set_global_error(const char* msg) { g_create_error = msg; }
+
 // ============================================================================
 // C ABI
 // ============================================================================

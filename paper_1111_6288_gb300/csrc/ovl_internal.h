@@ -108,6 +108,9 @@ void combine(const void* A, long long strideA, int na, const double2* d_C, int l
 // Partial-sum buffer size (double2 elements) needed by dot_rhs/norm2_rhs.
 constexpr int kRedBlocks = 608;
 
+// Message returned by ov_last_error(NULL) (errors of calls that have no context).
+void set_global_error(const char* msg);
+
 // ---- host linear algebra: hostla.cpp --------------------------------------
 // Column-major complex matrices as std::vector<double2>-compatible arrays of (re, im).
 struct HostCplx { double re, im; };
