@@ -113,8 +113,8 @@ typedef struct ov_profile {
     long long clenshaw_regions;  /* loops recorded (one per sign application call) */
     long long clenshaw_launches; /* Wilson-kernel launches inside them */
     double clenshaw_bytes;       /* algorithmic bytes of those launches: per launch and site,
-                                    the 4 links once plus every input, output and epilogue
-                                    spinor of each system */
+                                    the 4 links once (576 B FP64; 192 B FP32, two rows stored)
+                                    plus every input, output and epilogue spinor of each system */
     long long kernel_launches;   /* ov_launch_count() at the time of reading */
 } ov_profile;
 

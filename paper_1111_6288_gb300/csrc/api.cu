@@ -180,16 +180,6 @@ Bank* find_bank(ov_ctx* c, double phase) {
 
 // ---- small kernels local to the orchestration --------------------------------
 
-__global__ void proj_coeff_k(const double2* __restrict__ C, const double* __restrict__ signs, int n, int k,
-                             double2* __restrict__ Cneg, double2* __restrict__ Cs) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * k) return;
-    const int i = idx / k;
-    const double2 v = C[idx];
-    Cneg[idx] = make_double2(-v.x, -v.y);
-    Cs[idx] = make_double2(signs[i] * v.x, signs[i] * v.y);
-}
-
 template <typename R>
 __global__ void merge_sectors_k(const typename C2<R>::T* __restrict__ Y, const int* __restrict__ sys_of_rhs,
                                 typename C2<R>::T* __restrict__ out, long long n) {
@@ -294,17 +284,9 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
             any_bank = true;
             const int N = b->n;
             const void* Vb = std::is_same<R, double>::value ? b->V64 : b->V32;
-            TRY(ensure_small(c, 2LL * N * k, (long long)N * k * 4 * 152, ns));
-            multidot<R>(Vb, n12, N, src_j, n12, k, n12, c->d_C, c->d_partial, c->partial_cap, s);
-            CKL();
-            double2* Cneg = c->d_C2;
-            double2* Cs = c->d_C2 + (long long)N * k;
-            proj_coeff_k<<<(N * k + 127) / 128, 128, 0, s>>>(c->d_C, b->d_signs, N, k, Cneg, Cs);
-            count_launch();
-            CKL();
-            combine<R>(Vb, n12, N, Cneg, k, k, 1.0, src_j, n12, xp_j, n12, n12, s);
-            CKL();
-            combine<R>(Vb, n12, N, Cs, k, k, 0.0, nullptr, n12, ys_j, n12, n12, s);
+            TRY(ensure_small(c, 2LL * N * k, (long long)N * 4 * 4 * 152, ns));
+            small_space_project<R>(Vb, N, b->d_signs, src_j, k, xp_j, ys_j, n12, c->d_C, c->d_partial,
+                                   c->partial_cap, s);
             CKL();
         }
         j0 = j1;
@@ -333,11 +315,13 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     }
     // algorithmic bytes per site of one launch: links once (shared by the systems) plus each
     // system's input, output and epilogue vectors
+    // links: 36 complex FP64, 12 real-pairs (two rows) FP32; spinors 12 complex each
     const double esd = (double)sizeof(typename C2<R>::T), Vd = (double)V;
+    const double link_cplx = std::is_same<R, double>::value ? 36.0 : 24.0;
     for (int k = n - 1; k >= 0; --k) {
         if (c->profile) {
-            c->prof_bytes[prec] += Vd * esd * (36.0 + 24.0 * ns);                        // t = H_w b1
-            c->prof_bytes[prec] += Vd * esd * (36.0 + 12.0 * ns * (b2 ? 5.0 : 4.0));     // b_k
+            c->prof_bytes[prec] += Vd * esd * (link_cplx + 24.0 * ns);                     // t = H_w b1
+            c->prof_bytes[prec] += Vd * esd * (link_cplx + 12.0 * ns * (b2 ? 5.0 : 4.0));  // b_k
             c->prof_launches[prec] += 2;
         }
         launch_dslash<R>(c->g, m0, U, b1, t, ns, d_phase, plain, s);
@@ -524,7 +508,7 @@ int register_bank_internal(ov_ctx* c, double phase, const void* W64, int n, cons
     }
     CK(cudaMemcpy(b->d_signs, b->signs.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpyAsync(b->V64, W64, b64, cudaMemcpyDeviceToDevice, s));
-    launch_convert<double, float>(b->V64, b->V32, 12LL * c->g.V * n, s);
+    launch_convert<double, float>(b->V64, b->V32, c->g.V, n, s);
     CKL();
     return OV_OK;
 }
@@ -542,7 +526,7 @@ int cheb_filter(ov_ctx* c, void* W64, int m, double a, int degree, const double*
         W = W64;
     } else {
         TRY(workspace(c, "flt_W", prec, m, &W));
-        launch_convert<double, float>(W64, W, n, s);
+        launch_convert<double, float>(W64, W, c->g.V, m, s);
         CKL();
     }
     TRY(workspace(c, "flt_Tm", prec, m, &Tm));
@@ -577,7 +561,7 @@ int cheb_filter(ov_ctx* c, void* W64, int m, double a, int degree, const double*
     if (std::is_same<R, double>::value) {
         CK(cudaMemcpyAsync(W64, tk, vb * m, cudaMemcpyDeviceToDevice, s));
     } else {
-        launch_convert<float, double>(tk, W64, n, s);
+        launch_convert<float, double>(tk, W64, c->g.V, m, s);
         CKL();
     }
     return OV_OK;
@@ -715,7 +699,7 @@ int ov_set_gauge(ov_ctx* c, const void* U, int dtype, ov_stream_t stream) {
     const size_t n = 4ull * 9 * c->g.V;
     if (!c->U64) {
         if (cudaMalloc(&c->U64, n * sizeof(double2)) != cudaSuccess ||
-            cudaMalloc(&c->U32, n * sizeof(float2)) != cudaSuccess) {
+            cudaMalloc(&c->U32, 4ull * 3 * c->g.V * sizeof(float4)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, OV_ERR_OOM, "gauge field allocation failed");
         }
@@ -899,28 +883,63 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
 namespace {
 
 // CG on the chiral-sector normal operator A_s = P_s [2 (1 - m^2/4)(1 + s sign) + m^2] P_s for each
-// system (rhs vector B_k in sector chi_k), in precision R.  Y: solutions.
+// system (rhs vector B_k in sector chi_k), in precision R.  Y: solutions, in the order of S.
+// Converged systems leave the batch: the active ones are kept at the front (a converged
+// system is swapped with the last active one), so later sign applications run only on
+// systems that still iterate; Y is put back in the original order at the end.
 template <typename R>
-int inner_cg(ov_ctx* c, double mass, const SysSet& S, const void* B, void* Y, const std::vector<double>& tol_rel,
+int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, const std::vector<double>& tol_rel0,
              int max_iter, int* iters, cudaStream_t s) {
     const int prec = prec_of<R>();
-    const int ns = S.n;
+    const int ns = S0.n;
     const long long n12 = 12LL * c->g.V;
-    void *r, *p, *Ap;
+    void *r, *p, *Ap, *tmp;
     TRY(workspace(c, "cg_r", prec, ns, &r));
     TRY(workspace(c, "cg_p", prec, ns, &p));
     TRY(workspace(c, "cg_Ap", prec, ns, &Ap));
-    const size_t bytes = vec_bytes(c, prec) * ns;
+    TRY(workspace(c, "cg_tmp", prec, ns, &tmp));
+    const size_t vb = vec_bytes(c, prec);
+    const size_t bytes = vb * ns;
     CK(cudaMemcpyAsync(r, B, bytes, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p, B, bytes, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(Y, 0, bytes, s));
     TRY(ensure_small(c, 0, (long long)kRedBlocks * ns, ns));
+    SysSet S = S0;
+    std::vector<double> tol_rel = tol_rel0;
+    std::vector<int> perm(ns);
+    std::iota(perm.begin(), perm.end(), 0);
     std::vector<double> rr(ns), rr_new(ns), b2(ns), alpha(ns), beta(ns), ones(ns, 1.0);
     std::vector<double2> pap(ns);
     norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
     b2 = rr;
-    std::vector<char> active(ns);
-    for (int k = 0; k < ns; ++k) active[k] = rr[k] > 0.0;
+    auto swap_vec = [&](void* base, int i, int j) -> int {
+        char* bi = (char*)base + (size_t)i * vb;
+        char* bj = (char*)base + (size_t)j * vb;
+        CK(cudaMemcpyAsync(tmp, bi, vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bi, bj, vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bj, tmp, vb, cudaMemcpyDeviceToDevice, s));
+        return OV_OK;
+    };
+    // drop position k from the active front [0, na)
+    auto retire = [&](int k, int& na) -> int {
+        const int last = na - 1;
+        if (k != last) {
+            TRY(swap_vec(r, k, last));
+            TRY(swap_vec(p, k, last));
+            TRY(swap_vec(Y, k, last));
+            std::swap(perm[k], perm[last]);
+            std::swap(rr[k], rr[last]);
+            std::swap(b2[k], b2[last]);
+            std::swap(tol_rel[k], tol_rel[last]);
+            std::swap(S.phase[k], S.phase[last]);
+            std::swap(S.chi[k], S.chi[last]);
+        }
+        --na;
+        return OV_OK;
+    };
+    int na = ns;
+    for (int k = na - 1; k >= 0; --k)
+        if (!(rr[k] > 0.0)) TRY(retire(k, na));
     const double k1 = 2.0 * (1.0 - 0.25 * mass * mass);
     Epilogue fin;
     fin.c_op = k1 / c->hw_norm;
@@ -929,43 +948,46 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S, const void* B, void* Y, co
     fin.c2 = k1 + mass * mass;
     fin.v2 = p;
     int it = 0;
-    for (it = 0; it < max_iter; ++it) {
-        bool any = false;
-        for (int k = 0; k < ns; ++k) any = any || active[k];
-        if (!any) break;
-        TRY(sign_pipeline<R>(c, p, S, false, fin, Ap, s));
-        dot_rhs<R>(p, Ap, n12, ns, pap.data(), c->d_partial, c->d_red, s);
-        for (int k = 0; k < ns; ++k) {
-            if (!active[k]) {
-                alpha[k] = 0.0;
-                continue;
-            }
+    for (it = 0; it < max_iter && na > 0; ++it) {
+        SysSet A;
+        A.n = na;
+        A.phase.assign(S.phase.begin(), S.phase.begin() + na);
+        A.chi.assign(S.chi.begin(), S.chi.begin() + na);
+        TRY(sign_pipeline<R>(c, p, A, false, fin, Ap, s));
+        dot_rhs<R>(p, Ap, n12, na, pap.data(), c->d_partial, c->d_red, s);
+        for (int k = 0; k < na; ++k) {
             if (!std::isfinite(pap[k].x) || !std::isfinite(rr[k]))
-                return fail(c, OV_ERR_NAN, "inner CG: NaN/Inf in <p, A p> (system %d, iteration %d)", k, it);
+                return fail(c, OV_ERR_NAN, "inner CG: NaN/Inf in <p, A p> (system %d, iteration %d)", perm[k], it);
             if (pap[k].x <= 0.0)
                 return fail(c, OV_ERR_BREAKDOWN, "inner CG: <p, A p> = %g <= 0 (system %d, iteration %d)", pap[k].x,
-                            k, it);
+                            perm[k], it);
             alpha[k] = rr[k] / pap[k].x;
         }
-        launch_cg_xr<R>(alpha.data(), p, Ap, Y, r, n12, ns, s);
+        launch_cg_xr<R>(alpha.data(), p, Ap, Y, r, n12, na, s);
         CKL();
-        norm2_rhs<R>(r, n12, ns, rr_new.data(), c->d_partial, c->d_red, s);
-        for (int k = 0; k < ns; ++k) {
-            if (!active[k]) {
-                beta[k] = 0.0;
-                continue;
-            }
-            if (std::sqrt(rr_new[k]) <= tol_rel[k] * std::sqrt(b2[k])) active[k] = 0;
+        norm2_rhs<R>(r, n12, na, rr_new.data(), c->d_partial, c->d_red, s);
+        for (int k = 0; k < na; ++k) {
             beta[k] = rr_new[k] / rr[k];
             rr[k] = rr_new[k];
         }
-        launch_axpby<R>(ones.data(), r, beta.data(), p, n12, ns, s);  // p = r + beta p
+        launch_axpby<R>(ones.data(), r, beta.data(), p, n12, na, s);  // p = r + beta p
         CKL();
+        for (int k = na - 1; k >= 0; --k)
+            if (std::sqrt(rr[k]) <= tol_rel[k] * std::sqrt(b2[k])) TRY(retire(k, na));
     }
     *iters = it;
-    for (int k = 0; k < ns; ++k)
-        if (active[k]) return OV_ERR_NOT_CONVERGED;
-    return OV_OK;
+    // back to the original order: position k holds system perm[k]
+    bool moved = false;
+    for (int k = 0; k < ns; ++k) moved = moved || perm[k] != k;
+    if (moved) {
+        void* Yo;
+        TRY(workspace(c, "cg_yorder", prec, ns, &Yo));
+        for (int k = 0; k < ns; ++k)
+            CK(cudaMemcpyAsync((char*)Yo + (size_t)perm[k] * vb, (char*)Y + (size_t)k * vb, vb,
+                               cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(Y, Yo, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return na > 0 ? OV_ERR_NOT_CONVERGED : OV_OK;
 }
 
 template <typename R>
@@ -1053,7 +1075,8 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         int ns = 0;
         for (int k = 0; k < ns0; ++k) {
             const int j = src[k];
-            if (!(sn2[k] > 0.0)) continue;
+            // a sector whose residual is below a quarter of the target cannot matter
+            if (!(sn2[k] > 0.0) || std::sqrt(sn2[k]) <= 0.25 * tol * std::sqrt(bn2[j])) continue;
             if (ns != k)
                 CK(cudaMemcpyAsync((char*)S64 + (size_t)ns * vb64, (char*)S64 + (size_t)k * vb64, vb64,
                                    cudaMemcpyDeviceToDevice, s));
@@ -1068,7 +1091,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         if (std::is_same<R, double>::value)
             CK(cudaMemcpyAsync(Bs, S64, vb64 * ns, cudaMemcpyDeviceToDevice, s));
         else
-            launch_convert<double, R>(S64, Bs, n12 * ns, s);
+            launch_convert<double, float>(S64, Bs, V, ns, s);
         CKL();
         int iters = 0;
         int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s);
@@ -1090,7 +1113,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         if (std::is_same<R, double>::value)
             CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
         else
-            launch_convert<R, double>(E, E64, n12 * nrhs, s);
+            launch_convert<float, double>(E, E64, V, nrhs, s);
         launch_axpby<double>(ones.data(), E64, ones.data(), X, n12, nrhs, s);
         CKL();
         ++outer;

@@ -10,6 +10,9 @@
 // kernel adds the partials of each output in a fixed order.  Partial sums are
 // accumulated in FP64 for FP64 data and in FP32 within a thread for FP32 data,
 // then in FP64 across threads and blocks.
+#include <algorithm>
+#include <type_traits>
+
 #include "ovl_internal.h"
 
 namespace ovl {
@@ -51,66 +54,117 @@ __device__ double2 block_sum(double2 v) {
     return r;
 }
 
+// ---- per-site spinor access in the internal layouts ------------------------
+// FP64: 12 planes of double2; FP32: 6 planes of float4 holding components (2q, 2q+1).
+template <typename R> struct SiteIO;
+template <> struct SiteIO<double> {
+    typedef double2 T;
+    static __device__ __forceinline__ void load(const void* b, long long V, long long s, T (&p)[12]) {
+        const T* q = (const T*)b;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k] = q[k * V + s];
+    }
+    static __device__ __forceinline__ void store(void* b, long long V, long long s, const T (&p)[12]) {
+        T* q = (T*)b;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k * V + s] = p[k];
+    }
+};
+template <> struct SiteIO<float> {
+    typedef float2 T;
+    static __device__ __forceinline__ void load(const void* b, long long V, long long s, T (&p)[12]) {
+        const float4* q = (const float4*)b;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float4 v = q[j * V + s];
+            p[2 * j] = make_float2(v.x, v.y);
+            p[2 * j + 1] = make_float2(v.z, v.w);
+        }
+    }
+    static __device__ __forceinline__ void store(void* b, long long V, long long s, const T (&p)[12]) {
+        float4* q = (float4*)b;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) q[j * V + s] = make_float4(p[2 * j].x, p[2 * j].y, p[2 * j + 1].x, p[2 * j + 1].y);
+    }
+};
+
 // ---- packing -------------------------------------------------------------
 
 template <typename TI, typename R>
-__global__ void pack_spinor_k(const TI* __restrict__ abi, typename C2<R>::T* __restrict__ out, int V, int nrhs) {
+__global__ void pack_spinor_k(const TI* __restrict__ abi, void* __restrict__ out, int V, int nrhs) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)V * nrhs) return;
     const int r = (int)(idx / V), s = (int)(idx % V);
     const TI* src = abi + ((long long)r * V + s) * 12;
-    typename C2<R>::T* dst = out + (long long)r * 12 * V + s;
+    typename SiteIO<R>::T p[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        typename C2<R>::T v;
-        v.x = (R)src[k].x;
-        v.y = (R)src[k].y;
-        dst[(long long)k * V] = v;
+        p[k].x = (R)src[k].x;
+        p[k].y = (R)src[k].y;
     }
+    SiteIO<R>::store((char*)out + (long long)r * 12 * V * sizeof(typename SiteIO<R>::T), V, s, p);
 }
 
 template <typename R, typename TO>
-__global__ void unpack_spinor_k(const typename C2<R>::T* __restrict__ in, TO* __restrict__ abi, int V, int nrhs) {
+__global__ void unpack_spinor_k(const void* __restrict__ in, TO* __restrict__ abi, int V, int nrhs) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)V * nrhs) return;
     const int r = (int)(idx / V), s = (int)(idx % V);
-    const typename C2<R>::T* src = in + (long long)r * 12 * V + s;
+    typename SiteIO<R>::T p[12];
+    SiteIO<R>::load((const char*)in + (long long)r * 12 * V * sizeof(typename SiteIO<R>::T), V, s, p);
     TO* dst = abi + ((long long)r * V + s) * 12;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        typename C2<R>::T v = src[(long long)k * V];
         TO o;
-        o.x = v.x;
-        o.y = v.y;
+        o.x = p[k].x;
+        o.y = p[k].y;
         dst[k] = o;
     }
 }
 
-template <typename TI, typename R>
-__global__ void pack_gauge_k(const TI* __restrict__ abi, typename C2<R>::T* __restrict__ out, int V) {
+// FP64 links: 9 planes of double2 per direction.  FP32 links: rows 0 and 1 of U in
+// 3 planes of float4 per direction (entries (0,0)(0,1) | (0,2)(1,0) | (1,1)(1,2)); the
+// Wilson kernel rebuilds row 2 = conj(row0 x row1), exact for SU(3) links.
+template <typename TI>
+__global__ void pack_gauge64_k(const TI* __restrict__ abi, double2* __restrict__ out, int V) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 4LL * V) return;
     const int mu = (int)(idx / V), s = (int)(idx % V);
     const TI* src = abi + ((long long)mu * V + s) * 9;
-    typename C2<R>::T* dst = out + (long long)mu * 9 * V + s;
+    double2* dst = out + (long long)mu * 9 * V + s;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        typename C2<R>::T v;
-        v.x = (R)src[k].x;
-        v.y = (R)src[k].y;
-        dst[(long long)k * V] = v;
-    }
+    for (int k = 0; k < 9; ++k) dst[(long long)k * V] = make_double2((double)src[k].x, (double)src[k].y);
 }
 
+template <typename TI>
+__global__ void pack_gauge32_k(const TI* __restrict__ abi, float4* __restrict__ out, int V) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4LL * V) return;
+    const int mu = (int)(idx / V), s = (int)(idx % V);
+    const TI* src = abi + ((long long)mu * V + s) * 9;
+    float4* dst = out + (long long)mu * 3 * V + s;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        dst[(long long)q * V] = make_float4((float)src[2 * q].x, (float)src[2 * q].y, (float)src[2 * q + 1].x,
+                                            (float)src[2 * q + 1].y);
+}
+
+// spinor vectors between precisions (and so between the two internal layouts)
 template <typename RI, typename RO>
-__global__ void convert_k(const typename C2<RI>::T* __restrict__ in, typename C2<RO>::T* __restrict__ out,
-                          long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        typename C2<RI>::T v = in[i];
-        typename C2<RO>::T o;
-        o.x = (RO)v.x;
-        o.y = (RO)v.y;
-        out[i] = o;
+__global__ void convert_k(const void* __restrict__ in, void* __restrict__ out, int V, long long nvec) {
+    const long long total = (long long)V * nvec;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / V, s = i % V;
+        typename SiteIO<RI>::T p[12];
+        typename SiteIO<RO>::T o[12];
+        SiteIO<RI>::load((const char*)in + r * 12 * V * sizeof(typename SiteIO<RI>::T), V, s, p);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            o[k].x = (RO)p[k].x;
+            o[k].y = (RO)p[k].y;
+        }
+        SiteIO<RO>::store((char*)out + r * 12 * V * sizeof(typename SiteIO<RO>::T), V, s, o);
     }
 }
 
@@ -208,40 +262,37 @@ __global__ void scale_k(R a, const typename C2<R>::T* __restrict__ x, typename C
 
 // y_j = P_chi_j x_{src_j}: keeps spins 0,1 (chi = +1) or 2,3 (chi = -1).
 template <typename R>
-__global__ void chiral_split_k(const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
-                               const int* __restrict__ src, const signed char* __restrict__ chi, int V) {
+__global__ void chiral_split_k(const void* __restrict__ x, void* __restrict__ y, const int* __restrict__ src,
+                               const signed char* __restrict__ chi, int V) {
     const int j = blockIdx.y;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
-    const long long V12 = 12LL * V;
-    const typename C2<R>::T* px = x + (long long)src[j] * V12;
-    typename C2<R>::T* py = y + (long long)j * V12;
+    const size_t vb = (size_t)12 * V * sizeof(typename SiteIO<R>::T);
+    typename SiteIO<R>::T p[12];
+    SiteIO<R>::load((const char*)x + (size_t)src[j] * vb, V, s, p);
     const int c = chi[j];
-    typename C2<R>::T zero;
-    zero.x = 0;
-    zero.y = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
         const bool keep = (k < 6) ? (c > 0) : (c < 0);
-        py[(long long)k * V + s] = keep ? px[(long long)k * V + s] : zero;
+        if (!keep) p[k].x = p[k].y = 0;
     }
+    SiteIO<R>::store((char*)y + (size_t)j * vb, V, s, p);
 }
 
 template <typename R>
-__global__ void gamma5_k(const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y, int V) {
+__global__ void gamma5_k(const void* __restrict__ x, void* __restrict__ y, int V) {
     const int r = blockIdx.y;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
-    const long long o = (long long)r * 12 * V;
+    const size_t vb = (size_t)12 * V * sizeof(typename SiteIO<R>::T);
+    typename SiteIO<R>::T p[12];
+    SiteIO<R>::load((const char*)x + (size_t)r * vb, V, s, p);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        typename C2<R>::T v = x[o + (long long)k * V + s];
-        if (k >= 6) {
-            v.x = -v.x;
-            v.y = -v.y;
-        }
-        y[o + (long long)k * V + s] = v;
+    for (int k = 6; k < 12; ++k) {
+        p[k].x = -p[k].x;
+        p[k].y = -p[k].y;
     }
+    SiteIO<R>::store((char*)y + (size_t)r * vb, V, s, p);
 }
 
 // ---- multidot (split-K A^+ B) ----------------------------------------------
@@ -346,6 +397,113 @@ __global__ void __launch_bounds__(256) combine_k(const typename C2<R>::T* __rest
     }
 }
 
+// ---- small-space projection for a few right-hand sides ---------------------
+//
+// C[i][j] = <V_i, X_j> for j < nb <= SP_NB: each warp owns 8 rows of V and walks a
+// chunk of the element range, so every element of V is read once; each lane keeps
+// 8 x nb partial sums (in R), reduced across the warp in a fixed order and written
+// per chunk (the chunks are added by multidot_sum_k, also in a fixed order).
+constexpr int SP_NB = 4;
+constexpr int SP_ROWS = 8;  // rows per warp; 8 warps -> 64 rows per block
+
+template <typename R, int NB>
+__global__ void __launch_bounds__(256) vdot_rows_k(const typename C2<R>::T* __restrict__ V, long long sV, int na,
+                                                   const typename C2<R>::T* __restrict__ X, long long sX, int nb,
+                                                   long long n, long long chunk, double2* __restrict__ partial) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.y * 64 + warp * SP_ROWS;
+    const long long k_begin = (long long)blockIdx.x * chunk;
+    const long long k_end = min(n, k_begin + chunk);
+    R ar[SP_ROWS][NB], ai[SP_ROWS][NB];
+#pragma unroll
+    for (int r = 0; r < SP_ROWS; ++r)
+#pragma unroll
+        for (int j = 0; j < NB; ++j) ar[r][j] = ai[r][j] = 0;
+    for (long long m = k_begin + lane; m < k_end; m += 32) {
+        typename C2<R>::T xv[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j < nb) xv[j] = X[(long long)j * sX + m];
+            else xv[j].x = xv[j].y = 0;
+        }
+#pragma unroll
+        for (int r = 0; r < SP_ROWS; ++r) {
+            const int i = row0 + r;
+            if (i < na) {
+                const typename C2<R>::T v = V[(long long)i * sV + m];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {  // conj(v) * x
+                    ar[r][j] += v.x * xv[j].x + v.y * xv[j].y;
+                    ai[r][j] += v.x * xv[j].y - v.y * xv[j].x;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < SP_ROWS; ++r)
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            double re = (double)ar[r][j], im = (double)ai[r][j];
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_down_sync(0xffffffffu, re, o);
+                im += __shfl_down_sync(0xffffffffu, im, o);
+            }
+            const int i = row0 + r;
+            if (lane == 0 && i < na && j < nb) partial[((long long)blockIdx.x * na + i) * nb + j] = make_double2(re, im);
+        }
+}
+
+// Xp_j = X_j - sum_i V_i C[i][j],  Ys_j = sum_i V_i s_i C[i][j]  (j0 <= j < j0 + nj, nj <= SP_NB),
+// one pass over V; the coefficients are staged in shared memory in the precision R.
+template <typename R, int NB>
+__global__ void __launch_bounds__(256) proj_apply_k(const typename C2<R>::T* __restrict__ V, long long sV, int na,
+                                                    const double2* __restrict__ C, int ldc, const double* __restrict__ sg,
+                                                    int j0, int nj, const typename C2<R>::T* __restrict__ X,
+                                                    typename C2<R>::T* __restrict__ Xp, typename C2<R>::T* __restrict__ Ys,
+                                                    long long sX, long long n) {
+    extern __shared__ unsigned char sp_raw[];
+    typename C2<R>::T* cn = (typename C2<R>::T*)sp_raw;  // [na][NB]  -C
+    typename C2<R>::T* cs = cn + (size_t)na * NB;     // [na][NB]  s C
+    for (int q = threadIdx.x; q < na * NB; q += blockDim.x) {
+        const int i = q / NB, j = q % NB;
+        const double2 c = (j < nj) ? C[(long long)i * ldc + j0 + j] : make_double2(0, 0);
+        cn[q].x = (R)(-c.x);
+        cn[q].y = (R)(-c.y);
+        cs[q].x = (R)(sg[i] * c.x);
+        cs[q].y = (R)(sg[i] * c.y);
+    }
+    __syncthreads();
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+        R a1r[NB], a1i[NB], a2r[NB], a2i[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) a1r[j] = a1i[j] = a2r[j] = a2i[j] = 0;
+        for (int i = 0; i < na; ++i) {
+            const typename C2<R>::T v = V[(long long)i * sV + m];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const typename C2<R>::T c1 = cn[i * NB + j], c2 = cs[i * NB + j];
+                a1r[j] += v.x * c1.x - v.y * c1.y;
+                a1i[j] += v.x * c1.y + v.y * c1.x;
+                a2r[j] += v.x * c2.x - v.y * c2.y;
+                a2i[j] += v.x * c2.y + v.y * c2.x;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j < nj) {
+                const long long o = (long long)(j0 + j) * sX + m;
+                typename C2<R>::T xv = X[o], p, y;
+                p.x = xv.x + a1r[j];
+                p.y = xv.y + a1i[j];
+                y.x = a2r[j];
+                y.y = a2i[j];
+                Xp[o] = p;
+                Ys[o] = y;
+            }
+        }
+    }
+}
+
 inline int grid_for(long long n, int bs, int cap = 152 * 16) {
     long long g = (n + bs - 1) / bs;
     if (g > cap) g = cap;
@@ -362,9 +520,9 @@ void launch_pack_spinor(const void* abi, int dtype_in, void* internal, int V, in
     const long long n = (long long)V * nrhs;
     const int g = (int)((n + 255) / 256);
     if (dtype_in == 0)
-        pack_spinor_k<double2, R><<<g, 256, 0, s>>>((const double2*)abi, (typename C2<R>::T*)internal, V, nrhs);
+        pack_spinor_k<double2, R><<<g, 256, 0, s>>>((const double2*)abi, internal, V, nrhs);
     else
-        pack_spinor_k<float2, R><<<g, 256, 0, s>>>((const float2*)abi, (typename C2<R>::T*)internal, V, nrhs);
+        pack_spinor_k<float2, R><<<g, 256, 0, s>>>((const float2*)abi, internal, V, nrhs);
     count_launch();
 }
 
@@ -373,9 +531,9 @@ void launch_unpack_spinor(const void* internal, void* abi, int dtype_out, int V,
     const long long n = (long long)V * nrhs;
     const int g = (int)((n + 255) / 256);
     if (dtype_out == 0)
-        unpack_spinor_k<R, double2><<<g, 256, 0, s>>>((const typename C2<R>::T*)internal, (double2*)abi, V, nrhs);
+        unpack_spinor_k<R, double2><<<g, 256, 0, s>>>(internal, (double2*)abi, V, nrhs);
     else
-        unpack_spinor_k<R, float2><<<g, 256, 0, s>>>((const typename C2<R>::T*)internal, (float2*)abi, V, nrhs);
+        unpack_spinor_k<R, float2><<<g, 256, 0, s>>>(internal, (float2*)abi, V, nrhs);
     count_launch();
 }
 
@@ -383,16 +541,19 @@ template <typename R>
 void launch_pack_gauge(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s) {
     const long long n = 4LL * V;
     const int g = (int)((n + 255) / 256);
-    if (dtype_in == 0)
-        pack_gauge_k<double2, R><<<g, 256, 0, s>>>((const double2*)abi, (typename C2<R>::T*)internal, V);
-    else
-        pack_gauge_k<float2, R><<<g, 256, 0, s>>>((const float2*)abi, (typename C2<R>::T*)internal, V);
+    if (std::is_same<R, double>::value) {
+        if (dtype_in == 0) pack_gauge64_k<double2><<<g, 256, 0, s>>>((const double2*)abi, (double2*)internal, V);
+        else pack_gauge64_k<float2><<<g, 256, 0, s>>>((const float2*)abi, (double2*)internal, V);
+    } else {
+        if (dtype_in == 0) pack_gauge32_k<double2><<<g, 256, 0, s>>>((const double2*)abi, (float4*)internal, V);
+        else pack_gauge32_k<float2><<<g, 256, 0, s>>>((const float2*)abi, (float4*)internal, V);
+    }
     count_launch();
 }
 
 template <typename RI, typename RO>
-void launch_convert(const void* in, void* out, long long n, cudaStream_t s) {
-    convert_k<RI, RO><<<grid_for(n, 256), 256, 0, s>>>((const typename C2<RI>::T*)in, (typename C2<RO>::T*)out, n);
+void launch_convert(const void* in, void* out, int V, long long nvec, cudaStream_t s) {
+    convert_k<RI, RO><<<grid_for((long long)V * nvec, 256), 256, 0, s>>>(in, out, V, nvec);
     count_launch();
 }
 
@@ -455,14 +616,14 @@ template <typename R>
 void launch_chiral_split(const void* x, void* y, const int* src, const signed char* chi, int V, int nsys,
                          cudaStream_t s) {
     dim3 grid((V + 127) / 128, nsys);
-    chiral_split_k<R><<<grid, 128, 0, s>>>((const typename C2<R>::T*)x, (typename C2<R>::T*)y, src, chi, V);
+    chiral_split_k<R><<<grid, 128, 0, s>>>(x, y, src, chi, V);
     count_launch();
 }
 
 template <typename R>
 void launch_gamma5(const void* x, void* y, int V, int nrhs, cudaStream_t s) {
     dim3 grid((V + 127) / 128, nrhs);
-    gamma5_k<R><<<grid, 128, 0, s>>>((const typename C2<R>::T*)x, (typename C2<R>::T*)y, V);
+    gamma5_k<R><<<grid, 128, 0, s>>>(x, y, V);
     count_launch();
 }
 
@@ -500,6 +661,43 @@ void combine(const void* A, long long strideA, int na, const double2* d_C, int l
     }
 }
 
+template <typename R, int NB>
+void small_space_group(const void* V, int na, const double* d_signs, const void* X, int j0, int nj, void* Xp, void* Ys,
+                       long long n, double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s) {
+    typedef typename C2<R>::T T;
+    const int rowblocks = (na + 63) / 64;
+    long long nchunk = std::max(1LL, (4LL * 152) / rowblocks);
+    const long long cap = partial_cap / ((long long)na * nj);
+    if (nchunk > cap) nchunk = std::max(1LL, cap);
+    long long chunk = (n + nchunk - 1) / nchunk;
+    chunk = ((chunk + 31) / 32) * 32;
+    nchunk = (n + chunk - 1) / chunk;
+    dim3 grid((unsigned)nchunk, rowblocks);
+    vdot_rows_k<R, NB><<<grid, 256, 0, s>>>((const T*)V, n, na, (const T*)X + (long long)j0 * n, n, nj, n, chunk,
+                                            d_partial);
+    count_launch();
+    const int nab = na * nj;
+    multidot_sum_k<<<(nab + 255) / 256, 256, 0, s>>>(d_partial, (int)nchunk, nab, d_C);
+    count_launch();
+    const size_t shm = 2 * sizeof(T) * (size_t)na * NB;
+    proj_apply_k<R, NB><<<grid_for(n, 256, 152 * 8), 256, shm, s>>>((const T*)V, n, na, d_C, nj, d_signs, 0, nj,
+                                                                    (const T*)X + (long long)j0 * n,
+                                                                    (T*)Xp + (long long)j0 * n,
+                                                                    (T*)Ys + (long long)j0 * n, n, n);
+    count_launch();
+}
+
+template <typename R>
+void small_space_project(const void* V, int na, const double* d_signs, const void* X, int nb, void* Xp, void* Ys,
+                         long long n, double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s) {
+    for (int j0 = 0; j0 < nb; j0 += SP_NB) {
+        const int nj = std::min(SP_NB, nb - j0);
+        if (nj == 1) small_space_group<R, 1>(V, na, d_signs, X, j0, nj, Xp, Ys, n, d_C, d_partial, partial_cap, s);
+        else if (nj == 2) small_space_group<R, 2>(V, na, d_signs, X, j0, nj, Xp, Ys, n, d_C, d_partial, partial_cap, s);
+        else small_space_group<R, 4>(V, na, d_signs, X, j0, nj, Xp, Ys, n, d_C, d_partial, partial_cap, s);
+    }
+}
+
 #define OVL_INST(R)                                                                                                  \
     template void launch_pack_spinor<R>(const void*, int, void*, int, int, cudaStream_t);                           \
     template void launch_unpack_spinor<R>(const void*, void*, int, int, int, cudaStream_t);                         \
@@ -516,14 +714,14 @@ void combine(const void* A, long long strideA, int na, const double2* d_C, int l
     template void multidot<R>(const void*, long long, int, const void*, long long, int, long long, double2*,        \
                               double2*, long long, cudaStream_t);                                                  \
     template void combine<R>(const void*, long long, int, const double2*, int, int, double, const void*, long long, \
-                             void*, long long, long long, cudaStream_t);
+                             void*, long long, long long, cudaStream_t);                                           \
+    template void small_space_project<R>(const void*, int, const double*, const void*, int, void*, void*, long long, \
+                                         double2*, double2*, long long, cudaStream_t);
 OVL_INST(double)
 OVL_INST(float)
 #undef OVL_INST
 
-template void launch_convert<double, float>(const void*, void*, long long, cudaStream_t);
-template void launch_convert<float, double>(const void*, void*, long long, cudaStream_t);
-template void launch_convert<double, double>(const void*, void*, long long, cudaStream_t);
-template void launch_convert<float, float>(const void*, void*, long long, cudaStream_t);
+template void launch_convert<double, float>(const void*, void*, int, long long, cudaStream_t);
+template void launch_convert<float, double>(const void*, void*, int, long long, cudaStream_t);
 
 }  // namespace ovl

@@ -17,8 +17,15 @@
 // the fly per right-hand side; boundary factors multiply hops across the edge
 // and Dirichlet hops are skipped (no loads).
 //
+// Storage (see ovl_internal.h): FP64 spinors are 12 planes of double2 and links
+// 9 planes of double2 per direction; FP32 spinors are 6 planes of float4 (two
+// components per 16-byte load) and links keep their first two rows in 3 planes
+// of float4, the third row being rebuilt as conj(row0 x row1) (SU(3)).
+//
 // One thread per (site, rhs); each reads the 8 neighbour spinors, 8 links and
-// its own site for the mass term and the epilogue vectors.
+// its own site for the mass term and the epilogue vectors.  Threads of the same
+// site and different right-hand sides sit in the same block, so the links they
+// share are read from DRAM/L2 once and from L1 after.
 #include "ovl_internal.h"
 
 namespace ovl {
@@ -44,6 +51,8 @@ __device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
 }
 template <typename R>
 __device__ __forceinline__ Cx<R> cscale(R s, Cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> cconj(Cx<R> a) { return {a.re, -a.im}; }
 
 // Multiplication by the unit 1, i, -1, -i (code 0..3), resolved at compile time.
 template <int CODE, typename R>
@@ -64,20 +73,96 @@ template <> struct GBlock<1> { static constexpr bool diag = false; static conste
 template <> struct GBlock<2> { static constexpr bool diag = true; static constexpr int A = 3, B = 1; };   // -i s3
 template <> struct GBlock<3> { static constexpr bool diag = true; static constexpr int A = 0, B = 0; };   // 1
 
-template <typename R>
-__device__ __forceinline__ Cx<R> ld(const typename C2<R>::T* p, long long i) {
-    typename C2<R>::T v = __ldg(p + i);
-    return {v.x, v.y};
-}
+// ---- storage policies ------------------------------------------------------
+
+template <typename R> struct IO;
+
+template <> struct IO<double> {
+    // spinor: 12 planes of double2, component k = 3 spin + colour
+    static __device__ __forceinline__ void load(const void* base, long long V, int s, Cx<double> (&p)[12]) {
+        const double2* b = (const double2*)base;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 v = __ldg(b + k * V + s);
+            p[k] = {v.x, v.y};
+        }
+    }
+    static __device__ __forceinline__ void load_plain(const void* base, long long V, int s, Cx<double> (&p)[12]) {
+        const double2* b = (const double2*)base;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 v = b[k * V + s];
+            p[k] = {v.x, v.y};
+        }
+    }
+    static __device__ __forceinline__ void store(void* base, long long V, int s, const Cx<double> (&p)[12]) {
+        double2* b = (double2*)base;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) b[k * V + s] = make_double2(p[k].re, p[k].im);
+    }
+    // link U_mu(site): 9 planes of double2 per direction
+    static __device__ __forceinline__ void link(const void* U, long long V, int mu, int site, Cx<double> (&u)[3][3]) {
+        const double2* b = (const double2*)U + (long long)mu * 9 * V;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double2 v = __ldg(b + (i * 3 + j) * V + site);
+                u[i][j] = {v.x, v.y};
+            }
+    }
+};
+
+template <> struct IO<float> {
+    // spinor: 6 planes of float4 holding components (2p, 2p+1)
+    static __device__ __forceinline__ void load(const void* base, long long V, int s, Cx<float> (&p)[12]) {
+        const float4* b = (const float4*)base;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float4 v = __ldg(b + q * V + s);
+            p[2 * q] = {v.x, v.y};
+            p[2 * q + 1] = {v.z, v.w};
+        }
+    }
+    static __device__ __forceinline__ void load_plain(const void* base, long long V, int s, Cx<float> (&p)[12]) {
+        const float4* b = (const float4*)base;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float4 v = b[q * V + s];
+            p[2 * q] = {v.x, v.y};
+            p[2 * q + 1] = {v.z, v.w};
+        }
+    }
+    static __device__ __forceinline__ void store(void* base, long long V, int s, const Cx<float> (&p)[12]) {
+        float4* b = (float4*)base;
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            b[q * V + s] = make_float4(p[2 * q].re, p[2 * q].im, p[2 * q + 1].re, p[2 * q + 1].im);
+    }
+    // link: rows 0 and 1 in 3 planes of float4 per direction; row 2 = conj(row0 x row1)
+    static __device__ __forceinline__ void link(const void* U, long long V, int mu, int site, Cx<float> (&u)[3][3]) {
+        const float4* b = (const float4*)U + (long long)mu * 3 * V;
+        const float4 a0 = __ldg(b + site), a1 = __ldg(b + V + site), a2 = __ldg(b + 2 * V + site);
+        u[0][0] = {a0.x, a0.y};
+        u[0][1] = {a0.z, a0.w};
+        u[0][2] = {a1.x, a1.y};
+        u[1][0] = {a1.z, a1.w};
+        u[1][1] = {a2.x, a2.y};
+        u[1][2] = {a2.z, a2.w};
+        u[2][0] = cconj(csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1])));
+        u[2][1] = cconj(csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2])));
+        u[2][2] = cconj(csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0])));
+    }
+};
 
 template <typename R>
 struct Args {
-    const typename C2<R>::T* __restrict__ U;
-    const typename C2<R>::T* __restrict__ in;
-    typename C2<R>::T* out;
-    const typename C2<R>::T* v1;
-    const typename C2<R>::T* v2;
-    const typename C2<R>::T* v3;
+    const void* __restrict__ U;
+    const void* __restrict__ in;
+    void* out;
+    const void* v1;
+    const void* v2;
+    const void* v3;
     const double* phase;
     const signed char* chi;
     R c_op, c1, c2, c3, diag;
@@ -91,32 +176,26 @@ struct Args {
 // Accumulate one hop in direction MU: forward (FWD) uses U_mu(n) psi(n+mu) with
 // (1 - gamma_mu); backward uses U_mu(n-mu)^+ psi(n-mu) with (1 + gamma_mu).
 template <typename R, int MU, bool FWD>
-__device__ __forceinline__ void hop(const Args<R>& a, const typename C2<R>::T* __restrict__ in, int nb, int link_site,
-                                    Cx<R> fac, bool complex_fac, Cx<R> (&acc)[12]) {
+__device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, int link_site, Cx<R> fac,
+                                    bool complex_fac, Cx<R> (&acc)[12]) {
     constexpr int S = FWD ? 2 : 0;  // forward: h = psi_up - G psi_dn (multiply G by -1)
     using G = GBlock<MU>;
     const long long V = a.V;
+    Cx<R> p[12];
+    IO<R>::load(in, V, nb, p);
     Cx<R> h[2][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        Cx<R> p0 = ld<R>(in, 0 * 3 * V + c * V + nb);
-        Cx<R> p1 = ld<R>(in, 1 * 3 * V + c * V + nb);
-        Cx<R> p2 = ld<R>(in, 2 * 3 * V + c * V + nb);
-        Cx<R> p3 = ld<R>(in, 3 * 3 * V + c * V + nb);
         if constexpr (G::diag) {
-            h[0][c] = cadd(p0, mulu<G::A + S>(p2));
-            h[1][c] = cadd(p1, mulu<G::B + S>(p3));
+            h[0][c] = cadd(p[0 + c], mulu<G::A + S>(p[6 + c]));
+            h[1][c] = cadd(p[3 + c], mulu<G::B + S>(p[9 + c]));
         } else {
-            h[0][c] = cadd(p0, mulu<G::A + S>(p3));
-            h[1][c] = cadd(p1, mulu<G::B + S>(p2));
+            h[0][c] = cadd(p[0 + c], mulu<G::A + S>(p[9 + c]));
+            h[1][c] = cadd(p[3 + c], mulu<G::B + S>(p[6 + c]));
         }
     }
     Cx<R> u[3][3];
-    const typename C2<R>::T* Umu = a.U + (long long)MU * 9 * V;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) u[i][j] = ld<R>(Umu, (i * 3 + j) * V + link_site);
+    IO<R>::link(a.U, V, MU, link_site, u);
     Cx<R> w[2][3];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -146,13 +225,13 @@ __device__ __forceinline__ void hop(const Args<R>& a, const typename C2<R>::T* _
 }
 
 template <typename R, int MU>
-__device__ __forceinline__ void both_hops(const Args<R>& a, const typename C2<R>::T* __restrict__ in, int s,
-                                          const int (&x)[4], Cx<R> ph, Cx<R> (&acc)[12]) {
+__device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int s, int xmu, Cx<R> ph,
+                                          Cx<R> (&acc)[12]) {
     const int L = a.L[MU], st = a.stride[MU];
     // forward neighbour
     {
-        int nb = (x[MU] == L - 1) ? s - (L - 1) * st : s + st;
-        R f = (x[MU] == L - 1) ? a.bcf[MU] : R(1);
+        int nb = (xmu == L - 1) ? s - (L - 1) * st : s + st;
+        R f = (xmu == L - 1) ? a.bcf[MU] : R(1);
         if (f != R(0)) {
             if (MU == 0) hop<R, MU, true>(a, in, nb, s, {f * ph.re, f * ph.im}, true, acc);
             else hop<R, MU, true>(a, in, nb, s, {f, R(0)}, false, acc);
@@ -160,8 +239,8 @@ __device__ __forceinline__ void both_hops(const Args<R>& a, const typename C2<R>
     }
     // backward neighbour
     {
-        int nb = (x[MU] == 0) ? s + (L - 1) * st : s - st;
-        R f = (x[MU] == 0) ? a.bcf[MU] : R(1);
+        int nb = (xmu == 0) ? s + (L - 1) * st : s - st;
+        R f = (xmu == 0) ? a.bcf[MU] : R(1);
         if (f != R(0)) {
             if (MU == 0) hop<R, MU, false>(a, in, nb, nb, {f * ph.re, -f * ph.im}, true, acc);
             else hop<R, MU, false>(a, in, nb, nb, {f, R(0)}, false, acc);
@@ -169,48 +248,61 @@ __device__ __forceinline__ void both_hops(const Args<R>& a, const typename C2<R>
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) dslash_kernel(Args<R> a) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.V) return;
-    const int r = blockIdx.y;
-    const long long V = a.V;
-    const long long off = (long long)r * 12 * V;
-    const typename C2<R>::T* __restrict__ in = a.in + off;
+// Block = DSLASH_THREADS threads: all sites x 1 right-hand side, or half the sites x 2
+// right-hand sides when there are several, so that the threads of one site share the
+// SM's L1 for the site's links.  DSLASH_MIN_BLOCKS bounds the registers per thread.
+#ifndef OVL_DSLASH_THREADS
+#define OVL_DSLASH_THREADS 128
+#endif
+#ifndef OVL_DSLASH_MIN_BLOCKS
+#define OVL_DSLASH_MIN_BLOCKS 1
+#endif
 
-    int x[4];
-    {
-        int t = s;
-        x[0] = t % a.L[0]; t /= a.L[0];
-        x[1] = t % a.L[1]; t /= a.L[1];
-        x[2] = t % a.L[2]; t /= a.L[2];
-        x[3] = t;
-    }
+constexpr int DSLASH_THREADS = OVL_DSLASH_THREADS;
+
+template <typename R>
+__global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_kernel(Args<R> a, int nrhs) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (s >= a.V || r >= nrhs) return;
+    const long long V = a.V;
+    const long long off = (long long)r * 12 * V * (long long)sizeof(Cx<R>);  // bytes per right-hand side
+    const char* in = (const char*)a.in + off;
+
+    int t = s;
+    const int x0 = t % a.L[0];
+    t /= a.L[0];
+    const int x1 = t % a.L[1];
+    t /= a.L[1];
+    const int x2 = t % a.L[2];
+    const int x3 = t / a.L[2];
     Cx<R> ph = {R(1), R(0)};
     if (a.phase) {
         double sn, cs;
-        sincos(a.phase[r] * (double)x[3], &sn, &cs);
+        sincos(a.phase[r] * (double)x3, &sn, &cs);
         ph = {(R)cs, (R)sn};
     }
     Cx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-    both_hops<R, 0>(a, in, s, x, ph, acc);
-    both_hops<R, 1>(a, in, s, x, ph, acc);
-    both_hops<R, 2>(a, in, s, x, ph, acc);
-    both_hops<R, 3>(a, in, s, x, ph, acc);
+    both_hops<R, 0>(a, in, s, x0, ph, acc);
+    both_hops<R, 1>(a, in, s, x1, ph, acc);
+    both_hops<R, 2>(a, in, s, x2, ph, acc);
+    both_hops<R, 3>(a, in, s, x3, ph, acc);
 
     // z = c_op * gamma5 (diag psi - acc/2) + c1 v1
-    Cx<R> z[12];
+    Cx<R> z[12], tmp[12];
+    IO<R>::load(in, V, s, tmp);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        Cx<R> d = csub(cscale(a.diag, ld<R>(in, k * V + s)), cscale(R(0.5), acc[k]));
+        Cx<R> d = csub(cscale(a.diag, tmp[k]), cscale(R(0.5), acc[k]));
         if (k >= 6) d = {-d.re, -d.im};  // gamma5
         z[k] = cscale(a.c_op, d);
     }
     if (a.v1) {
+        IO<R>::load((const char*)a.v1 + off, V, s, tmp);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c1, ld<R>(a.v1 + off, k * V + s)));
+        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c1, tmp[k]));
     }
     if (a.g5) {
 #pragma unroll
@@ -229,25 +321,17 @@ __global__ void __launch_bounds__(128) dslash_kernel(Args<R> a) {
         }
     }
     if (a.v2) {
+        IO<R>::load((const char*)a.v2 + off, V, s, tmp);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c2, ld<R>(a.v2 + off, k * V + s)));
+        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c2, tmp[k]));
     }
     if (a.v3) {
-        // v3 may alias out: plain loads, same thread reads then writes element (k, s)
+        // v3 may alias out: plain loads; the same thread reads then writes site s
+        IO<R>::load_plain((const char*)a.v3 + off, V, s, tmp);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            typename C2<R>::T v = a.v3[off + k * V + s];
-            z[k] = cadd(z[k], cscale(a.c3, Cx<R>{v.x, v.y}));
-        }
+        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c3, tmp[k]));
     }
-    typename C2<R>::T* out = a.out + off;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        typename C2<R>::T v;
-        v.x = z[k].re;
-        v.y = z[k].im;
-        out[k * V + s] = v;
-    }
+    IO<R>::store((char*)a.out + off, V, s, z);
 }
 
 }  // namespace
@@ -255,14 +339,13 @@ __global__ void __launch_bounds__(128) dslash_kernel(Args<R> a) {
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
                    const double* d_phase, const Epilogue& e, cudaStream_t s) {
-    typedef typename C2<R>::T T;
     Args<R> a;
-    a.U = (const T*)links;
-    a.in = (const T*)in;
-    a.out = (T*)out;
-    a.v1 = (const T*)e.v1;
-    a.v2 = (const T*)e.v2;
-    a.v3 = (const T*)e.v3;
+    a.U = links;
+    a.in = in;
+    a.out = out;
+    a.v1 = e.v1;
+    a.v2 = e.v2;
+    a.v3 = e.v3;
     a.phase = d_phase;
     a.chi = e.chi;
     a.c_op = (R)e.c_op;
@@ -279,9 +362,10 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
     }
     a.V = g.V;
     a.g5 = e.g5;
-    dim3 block(128);
-    dim3 grid((g.V + 127) / 128, nrhs);
-    dslash_kernel<R><<<grid, block, 0, s>>>(a);
+    const int by = nrhs > 1 ? 2 : 1, bx = DSLASH_THREADS / by;
+    dim3 block(bx, by);
+    dim3 grid((g.V + bx - 1) / bx, (nrhs + by - 1) / by);
+    dslash_kernel<R><<<grid, block, 0, s>>>(a, nrhs);
     count_launch();
 }
 

@@ -1,11 +1,14 @@
 // Internal declarations of libovl: data layouts, kernel launchers, host helpers.
 //
 // Internal layouts (all site-major over the fastest index so that a warp reads
-// 32 consecutive sites of one component):
-//   spinor  [rhs][12][V]    complex<R>, component k = 3*spin + colour
-//   links   [4][9][V]       complex<R>, entry 3*a + b of U_mu(n)
-//   bank    [n_ev][12][V]   complex<R> (the same layout as a spinor)
-// with R = double (OV_PREC_F64) or float (OV_PREC_F32).
+// 32 consecutive sites of one component; component k = 3*spin + colour):
+//   FP64 spinor  [rhs][12][V] double2
+//   FP32 spinor  [rhs][6][V]  float4 = components (2q, 2q+1); spins 0,1 are planes 0-2
+//   FP64 links   [4][9][V]    double2, entry 3*a + b of U_mu(n)
+//   FP32 links   [4][3][V]    float4 = rows 0 and 1 of U_mu(n); row 2 = conj(row0 x row1)
+//   bank         [n_ev][...]  the spinor layout of its precision
+// A spinor vector is 12 V complex numbers (192 B or 96 B per site) in both precisions,
+// so element-wise kernels and inner products treat vectors as flat complex arrays.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -62,9 +65,9 @@ void launch_unpack_spinor(const void* internal, void* abi, int dtype_out, int V,
 // ABI links [4][site][3][3] -> internal [4][9][V] of R.
 template <typename R>
 void launch_pack_gauge(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s);
-// Element-wise conversion between precisions (same layout), n complex numbers.
+// Conversion of nvec spinor vectors between precisions (and internal layouts).
 template <typename RI, typename RO>
-void launch_convert(const void* in, void* out, long long n, cudaStream_t s);
+void launch_convert(const void* in, void* out, int V, long long nvec, cudaStream_t s);
 
 // Per-rhs reductions over n complex numbers each (vectors at stride n).  Results are
 // written to host memory after an internal synchronisation of s.  Deterministic.
@@ -104,6 +107,13 @@ void multidot(const void* A, long long strideA, int na, const void* B, long long
 template <typename R>
 void combine(const void* A, long long strideA, int na, const double2* d_C, int ldc, int nb, double alpha,
              const void* X, long long strideX, void* out, long long strideO, long long n, cudaStream_t s);
+
+// Small-space projection of nb vectors X (each n complex, stride n) on na bank vectors V:
+// C = V^+ X (device, [na][min(nb,4)] per group of 4), Xp = X - V C, Ys = V diag(signs) C.
+// Reads V twice per group of 4 right-hand sides.  na <= 384.
+template <typename R>
+void small_space_project(const void* V, int na, const double* d_signs, const void* X, int nb, void* Xp, void* Ys,
+                         long long n, double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s);
 
 // Partial-sum buffer size (double2 elements) needed by dot_rhs/norm2_rhs.
 constexpr int kRedBlocks = 608;
