@@ -283,6 +283,7 @@ def main():
     t0 = time.perf_counter()
     lam, V = P.eigensolve_Q(ctx_64, N_EV, tol=1e-10, max_iter=200, register=True, want_vectors=True)
     t_eig = time.perf_counter() - t0
+    eig_info = ctx_64.last_info
     P.deflate(ctx_mix, V, lam)
     del V
     # replicas solve different spin-colour point sources
@@ -419,7 +420,7 @@ def main():
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "setup": {"eigensolver_s": t_eig, "hw_norm": ctx_mix.hw_norm, "lambda_min": float(abs(lam).min()),
+            "setup": {"eigensolver_s": t_eig, "eigensolver": eig_info, "hw_norm": ctx_mix.hw_norm, "lambda_min": float(abs(lam).min()),
                       "lambda_max_in_bank": float(abs(lam).max())},
         }
         print(json.dumps(line))

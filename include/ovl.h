@@ -126,6 +126,8 @@ int ov_create(const ov_params* p, ov_ctx** out);
 int ov_destroy(ov_ctx* ctx);
 /* Message of the last failure on ctx (or of the last ov_create failure if ctx is NULL). */
 const char* ov_last_error(const ov_ctx* ctx);
+/* Human-readable summary of the last eigensolver call on ctx (cycles, residuals, time). */
+const char* ov_last_info(const ov_ctx* ctx);
 /* Number of lattice sites. */
 long long ov_volume(const ov_ctx* ctx);
 /* ||H_w|| in use (after the hw_norm <= 0 default is resolved). */

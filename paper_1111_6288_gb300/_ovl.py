@@ -70,6 +70,7 @@ _SIGNATURES = {
     "ov_create": (_I, [C.POINTER(_Params), C.POINTER(_VP)]),
     "ov_destroy": (_I, [_VP]),
     "ov_last_error": (C.c_char_p, [_VP]),
+    "ov_last_info": (C.c_char_p, [_VP]),
     "ov_volume": (C.c_longlong, [_VP]),
     "ov_hw_norm": (_D, [_VP]),
     "ov_set_gauge": (_I, [_VP, _VP, _I, _VP]),
@@ -194,6 +195,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    @property
+    def last_info(self):
+        """Summary of the last eigensolver call on this context."""
+        return lib().ov_last_info(self.handle).decode()
 
     @property
     def volume(self):

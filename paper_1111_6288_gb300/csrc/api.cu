@@ -51,6 +51,7 @@ struct ov_ctx {
     std::vector<double> coeffs;
     double hw_norm = 0.0;
     std::string err;
+    std::string info;  // summary of the last eigensolver / solve call
     void* U64 = nullptr;
     void* U32 = nullptr;
     bool gauge_set = false;
@@ -69,6 +70,10 @@ struct ov_ctx {
     long long dslash_count = 0;
     long long sign_count = 0;
     // optional CUDA-event timing of the Clenshaw loops (the Wilson kernels of the polynomial)
+    // CUDA graphs of the Clenshaw loop, keyed by precision, systems and buffers
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, std::pair<cudaGraphExec_t, void*>> graphs;  // exec, buffer holding p
     bool profile = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[2];  // per OV_PREC_*
     long long prof_launches[2] = {0, 0};
@@ -302,42 +307,70 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
     const double m0 = c->p.m0;
     const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
-    launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, s);
-    CKL();
-    void* b1 = bA;
-    void* b2 = nullptr;
-    Epilogue plain;
+    // algorithmic bytes per site of one launch: links once (shared by the systems) plus each
+    // system's input, output and epilogue vectors
+    const double esd = (double)sizeof(typename C2<R>::T), Vd = (double)V;
+    const double link_cplx = std::is_same<R, double>::value ? 36.0 : 24.0;
+    // the whole recurrence (2n launches, no host work) as one stream sequence
+    auto enqueue = [&](cudaStream_t st) -> void* {
+        launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, st);
+        void* b1 = bA;
+        void* b2 = nullptr;
+        Epilogue plain;
+        for (int k = n - 1; k >= 0; --k) {
+            launch_dslash<R>(c->g, m0, U, b1, t, ns, d_phase, plain, st);
+            Epilogue e;
+            const double half = (k == 0) ? 0.5 : 1.0;
+            e.c_op = alpha * half;
+            e.c1 = beta * half;
+            e.v1 = b1;
+            e.c2 = c->coeffs[k];
+            e.v2 = xperp;
+            e.c3 = -1.0;
+            e.v3 = b2;
+            void* o = b2 ? b2 : bB;
+            launch_dslash<R>(c->g, m0, U, t, o, ns, d_phase, e, st);
+            b2 = b1;
+            b1 = o;
+        }
+        return b1;
+    };
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (c->profile) {
         CK(cudaEventCreate(&ev0));
         CK(cudaEventCreate(&ev1));
         CK(cudaEventRecord(ev0, s));
-    }
-    // algorithmic bytes per site of one launch: links once (shared by the systems) plus each
-    // system's input, output and epilogue vectors
-    // links: 36 complex FP64, 12 real-pairs (two rows) FP32; spinors 12 complex each
-    const double esd = (double)sizeof(typename C2<R>::T), Vd = (double)V;
-    const double link_cplx = std::is_same<R, double>::value ? 36.0 : 24.0;
-    for (int k = n - 1; k >= 0; --k) {
-        if (c->profile) {
-            c->prof_bytes[prec] += Vd * esd * (link_cplx + 24.0 * ns);                     // t = H_w b1
-            c->prof_bytes[prec] += Vd * esd * (link_cplx + 12.0 * ns * (b2 ? 5.0 : 4.0));  // b_k
-            c->prof_launches[prec] += 2;
+        for (int k = n - 1; k >= 0; --k) {
+            c->prof_bytes[prec] += Vd * esd * (link_cplx + 24.0 * ns);                                  // t = H_w b1
+            c->prof_bytes[prec] += Vd * esd * (link_cplx + 12.0 * ns * (k == n - 1 ? 4.0 : 5.0));     // b_k
         }
-        launch_dslash<R>(c->g, m0, U, b1, t, ns, d_phase, plain, s);
-        Epilogue e;
-        const double half = (k == 0) ? 0.5 : 1.0;
-        e.c_op = alpha * half;
-        e.c1 = beta * half;
-        e.v1 = b1;
-        e.c2 = c->coeffs[k];
-        e.v2 = xperp;
-        e.c3 = -1.0;
-        e.v3 = b2;
-        void* o = b2 ? b2 : bB;
-        launch_dslash<R>(c->g, m0, U, t, o, ns, d_phase, e, s);
-        b2 = b1;
-        b1 = o;
+        c->prof_launches[prec] += 2LL * n;
+    }
+    void* b1 = nullptr;
+    if (c->use_graphs) {
+        char key[256];
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p", prec, ns, xperp, bA, bB, t, (const void*)d_phase, U);
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            void* res = enqueue(c->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &graph);
+            if (e1 != cudaSuccess || !graph)
+                return fail(c, OV_ERR_CUDA, "graph capture of the polynomial loop failed: %s", cudaGetErrorString(e1));
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e2 != cudaSuccess) return fail(c, OV_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
+            it = c->graphs.emplace(key, std::make_pair(exec, res)).first;
+            g_launches.fetch_sub(2LL * n + 1);  // counted at replay, not at capture
+        }
+        CK(cudaGraphLaunch(it->second.first, s));
+        count_launch(2LL * n + 1);
+        b1 = it->second.second;
+    } else {
+        b1 = enqueue(s);
     }
     CKL();
     if (c->profile) {
@@ -625,6 +658,8 @@ int ov_destroy(ov_ctx* c) {
         if (b.V32) cudaFree(b.V32);
         if (b.d_signs) cudaFree(b.d_signs);
     }
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& v : c->prof_events)
         for (auto& e : v) {
             cudaEventDestroy(e.first);
@@ -638,6 +673,8 @@ int ov_destroy(ov_ctx* c) {
 }
 
 const char* ov_last_error(const ov_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+const char* ov_last_info(const ov_ctx* c) { return c ? c->info.c_str() : ""; }
 
 long long ov_volume(const ov_ctx* c) { return c ? c->g.V : 0; }
 
@@ -764,7 +801,9 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     if (!(tol > 0.0)) return fail(c, OV_ERR_ARG, "tol must be > 0");
     if (!std::isfinite(phase)) return fail(c, OV_ERR_ARG, "non-finite phase");
     cudaStream_t s = (cudaStream_t)stream;
-    const int m = std::min(std::min(n_ev + std::max(16, n_ev / 2), 12 * c->g.V), kMaxRhs);
+    // block = wanted + guard; a deep guard puts the damping edge a beyond the cluster the
+    // wanted set ends in (near-degenerate modes at the cut converge at the rate set by a)
+    const int m = std::min(std::min(n_ev + std::max(16, n_ev), 12 * c->g.V), kMaxRhs);
     const long long n12 = 12LL * c->g.V;
     const size_t vb = vec_bytes(c, OV_PREC_F64);
     void *W, *W2, *QW, *QW2, *tt;
@@ -783,22 +822,32 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     TRY(upload_sys(c, S, s));
     const double* d_phase = phase != 0.0 ? c->d_phase : nullptr;
     const double h = c->hw_norm;
-    // The filter runs in FP32 while the residuals are far above FP32 resolution, then in FP64.
+    // The filter runs in FP32 while the residuals are well above FP32 resolution, then in FP64.
     // Its degree is chosen each cycle so that the largest amplification, |T_d(z(0))| with
     // z(0) = -(1 + a)/(1 - a), stays below amp: a larger spread between the filtered columns
     // would collapse the block below the resolution of the Cholesky-QR step.
-    const double switch_res = 3e-5;
+    const double switch_res = 3e-6;
+    double prev_worst = 1e300;
+    bool in_f64 = false;
     double a = -1.0;  // lower end of the damped interval of Q^2 (set by each Rayleigh-Ritz)
     std::vector<double> theta(m), res(m, 1e300);
     double worst = 1e300;
     int status = OV_ERR_NOT_CONVERGED;
     std::string hist;
+    bool last_lo = true;
+    int last_degree = 0;
+    const auto t_start = std::chrono::steady_clock::now();
     for (int it = 0; it <= max_iter; ++it) {
         if (it > 0) {
-            const bool lo = worst > switch_res;
+            // FP32 until the residual reaches switch_res or stops improving, then FP64
+            if (!in_f64 && (worst <= switch_res || (worst < 1e-4 && worst > 0.9 * prev_worst))) in_f64 = true;
+            prev_worst = worst;
+            const bool lo = !in_f64;
             const double amp = lo ? 1e3 : 1e6;
             const double z0 = (1.0 + a) / (1.0 - a);
             const int degree = std::max(2, std::min(200, (int)std::ceil(std::acosh(amp) / std::acosh(z0))));
+            last_lo = lo;
+            last_degree = degree;
             if (lo) TRY(cheb_filter<float>(c, W, m, a, degree, d_phase, s));
             else TRY(cheb_filter<double>(c, W, m, a, degree, d_phase, s));
             TRY(cholqr2(c, W, m, W2, s));
@@ -855,8 +904,9 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
         norm2_rhs<double>(tt, n12, n_ev, res.data(), c->d_partial, c->d_red, s);
         worst = 0.0;
         for (int i = 0; i < n_ev; ++i) worst = std::max(worst, std::sqrt(res[i]));
-        char buf[64];
-        snprintf(buf, sizeof(buf), "%s%.1e", it ? " " : "", worst);
+        char buf[96];
+        snprintf(buf, sizeof(buf), "%s%s%d:%.1e", it ? " " : "", it == 0 ? "" : (last_lo ? "f32/" : "f64/"),
+                 last_degree, worst);
         hist += buf;
         if (worst <= tol) {
             status = OV_OK;
@@ -870,6 +920,12 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     }
     if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
     CK(cudaStreamSynchronize(s));
+    {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "eigensolver: n_ev %d, block %d, %.1f s; per cycle [precision/degree:]worst residual: ",
+                 n_ev, m, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+        c->info = std::string(buf) + hist;
+    }
     if (status != OV_OK)
         return fail(c, status, "eigensolver: not converged after %d filter cycles; worst residual per cycle: %s",
                     max_iter, hist.c_str());
