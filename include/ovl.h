@@ -132,6 +132,8 @@ const char* ov_last_info(const ov_ctx* ctx);
 long long ov_volume(const ov_ctx* ctx);
 /* ||H_w|| in use (after the hw_norm <= 0 default is resolved). */
 double ov_hw_norm(const ov_ctx* ctx);
+/* delta = max over [eps, 1] of |1 - sqrt(x) P(x)| for the polynomial in use (Sec. 2, eq. 2). */
+double ov_poly_delta(const ov_ctx* ctx);
 
 /* Turn event timing of the polynomial loops on (on != 0) or off. */
 int ov_set_profiling(ov_ctx* ctx, int on);
@@ -229,6 +231,41 @@ int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_ite
  * sector), then the correction D(m)^+ y.  stats: host, may be NULL. */
 int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, void* x,
                   int nrhs, double tol, ov_solve_stats* stats, ov_stream_t stream);
+
+/* ---- derivatives with respect to the field (Sec. 4) --------------------- */
+/* The background field enters as the phase exp(i phi t) on the x links, phi = q E.  The
+ * paper takes energy shifts from correlators at several field values; these calls give
+ * the derivative of the operator, and with a solve, of the correlator, with respect to
+ * phi.  All arrays complex128, FP64 arithmetic, layouts as above. */
+
+/* out = dH_w/dphi in: the x hops with their phase factors differentiated (i t and -i t). */
+int ov_apply_dHdphi(ov_ctx* ctx, const void* in, void* out, int nrhs, const double* phase, ov_stream_t stream);
+
+/* out = dD(m)/dphi in = (1 - m/2) gamma5 dF/dphi in, F the implemented sign function
+ * (small space registered for each phase plus the polynomial).  dF is the Daleckii-Krein
+ * derivative in three blocks: the tangent of the Clenshaw recurrence on the large space
+ * (recomputed, nothing stored), (s_i - s_j)/(l_i - l_j) on the small space, and between
+ * them (s_i - sign(l))/(l_i - l) (the polynomial error delta below the exact divided
+ * difference), applied through per-bank vectors u_i built on first use: the opposite-sign
+ * part of the large-space component of dH v_i, times 1/(|t_i| + |Q|) as a Chebyshev
+ * polynomial in Q^2 per mode.  Accurate while delta is small against the gap at the cut.
+ * Synchronises the stream. */
+int ov_apply_dDdphi(ov_ctx* ctx, const void* in, void* out, int nrhs, double mass, const double* phase,
+                    ov_stream_t stream);
+
+/* Pion correlator C(t) = sum_rhs sum_{x,y,z} sum_{spin,colour} |S|^2 of propagator columns
+ * S (device [nrhs][site][4][3]); C: host [Lt].  Synchronises the stream. */
+int ov_correlator(ov_ctx* ctx, const void* S, int nrhs, double* C, ov_stream_t stream);
+
+/* out(x, t) = w(t) G in(x, t), G = gamma5 if gamma5 != 0 else 1; w: host [Lt]. */
+int ov_timeslice_scale(ov_ctx* ctx, const void* in, void* out, int nrhs, const double* w, int gamma5,
+                       ov_stream_t stream);
+
+/* Inner products <a_j, b_j> (conjugate-linear in a) of device vectors, per right-hand side
+ * (per_timeslice = 0; out: host [nrhs][2]) or per right-hand side and timeslice
+ * (per_timeslice != 0; out: host [nrhs][Lt][2]).  Deterministic. */
+int ov_inner(ov_ctx* ctx, const void* a, const void* b, int nrhs, int per_timeslice, double* out,
+             ov_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -22,15 +22,22 @@ from ._ovl import (  # noqa: F401
     OvlError,
     Params,
     SolveStats,
+    apply_dDdphi,
+    apply_dHdphi,
     apply_overlap,
     apply_sign_Hw,
     apply_wilson,
     chebyshev_coeffs,
+    correlator,
+    correlator_jacobian,
     deflate,
     eigensolve_Q,
     host_eigh,
+    inner,
     launch_count,
     lib,
     library_path,
+    pion_correlator,
     solve_overlap,
+    timeslice_scale,
 )

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "ov_last_info": (C.c_char_p, [_VP]),
     "ov_volume": (C.c_longlong, [_VP]),
     "ov_hw_norm": (_D, [_VP]),
+    "ov_poly_delta": (_D, [_VP]),
     "ov_set_gauge": (_I, [_VP, _VP, _I, _VP]),
     "ov_set_profiling": (_I, [_VP, _I]),
     "ov_read_profile": (_I, [_VP, _I, C.POINTER(_Profile)]),
@@ -86,6 +87,11 @@ _SIGNATURES = {
     "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
     "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
     "solve_overlap": (_I, [_VP, _D, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),
+    "ov_apply_dHdphi": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
+    "ov_apply_dDdphi": (_I, [_VP, _VP, _VP, _I, _D, _DP, _VP]),
+    "ov_correlator": (_I, [_VP, _VP, _I, _DP, _VP]),
+    "ov_timeslice_scale": (_I, [_VP, _VP, _VP, _I, _DP, _I, _VP]),
+    "ov_inner": (_I, [_VP, _VP, _VP, _I, _I, _DP, _VP]),
 }
 
 _lib = None
@@ -208,6 +214,11 @@ class Context:
     @property
     def hw_norm(self):
         return float(lib().ov_hw_norm(self.handle))
+
+    @property
+    def delta(self):
+        """Error |1 - sqrt(x) P(x)| of the polynomial in use, maximised over [eps, 1]."""
+        return float(lib().ov_poly_delta(self.handle))
 
     @property
     def site_shape(self):
@@ -371,3 +382,137 @@ def host_eigh(A):
     Z = np.zeros((n, n), dtype=np.complex128, order="F")
     _check(lib().ov_host_eigh(n, A.ctypes.data_as(_DP), w.ctypes.data_as(_DP), Z.ctypes.data_as(_DP)))
     return w, Z
+
+
+# ---------------------------------------------------------------------------
+# field derivatives and the pion correlator (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def apply_dHdphi(ctx: Context, x, out, phase=None, stream=None):
+    """out = dH_w/dphi x (complex128)."""
+    import torch
+
+    n = ctx._check_spinor(x, "x", dtype=torch.complex128)
+    ctx._check_spinor(out, "out", dtype=torch.complex128)
+    keep, ph = _phase_ptr(phase, n)
+    _check(lib().ov_apply_dHdphi(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, ph,
+                                 _stream(stream)), ctx.handle)
+    return out
+
+
+def apply_dDdphi(ctx: Context, x, out, mass, phase=None, stream=None):
+    """out = dD(m)/dphi x (complex128), through the small space and the polynomial."""
+    import torch
+
+    n = ctx._check_spinor(x, "x", dtype=torch.complex128)
+    ctx._check_spinor(out, "out", dtype=torch.complex128)
+    keep, ph = _phase_ptr(phase, n)
+    _check(lib().ov_apply_dDdphi(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, float(mass),
+                                 ph, _stream(stream)), ctx.handle)
+    return out
+
+
+def correlator(ctx: Context, S, stream=None):
+    """C(t) = sum over right-hand sides, space, spin and colour of |S|^2 (numpy [Lt])."""
+    import torch
+
+    n = ctx._check_spinor(S, "S", dtype=torch.complex128)
+    out = np.zeros(ctx.dims[3])
+    _check(lib().ov_correlator(ctx.handle, C.c_void_p(S.data_ptr()), n, out.ctypes.data_as(_DP), _stream(stream)),
+           ctx.handle)
+    return out
+
+
+def timeslice_scale(ctx: Context, x, out, w, gamma5=False, stream=None):
+    """out(t) = w(t) (gamma5) x(t)."""
+    import torch
+
+    n = ctx._check_spinor(x, "x", dtype=torch.complex128)
+    ctx._check_spinor(out, "out", dtype=torch.complex128)
+    wa, wp = _darr(w)
+    _check(lib().ov_timeslice_scale(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, wp,
+                                    int(gamma5), _stream(stream)), ctx.handle)
+    return out
+
+
+def inner(ctx: Context, a, b, per_timeslice=False, stream=None):
+    """<a_j, b_j> per right-hand side (numpy complex [nrhs]) or per (rhs, t) ([nrhs, Lt])."""
+    import torch
+
+    n = ctx._check_spinor(a, "a", dtype=torch.complex128)
+    ctx._check_spinor(b, "b", dtype=torch.complex128)
+    m = n * (ctx.dims[3] if per_timeslice else 1)
+    out = np.zeros(2 * m)
+    _check(lib().ov_inner(ctx.handle, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), n, int(per_timeslice),
+                          out.ctypes.data_as(_DP), _stream(stream)), ctx.handle)
+    z = out[0::2] + 1j * out[1::2]
+    return z.reshape(n, ctx.dims[3]) if per_timeslice else z
+
+
+def _solve_columns(ctx, b, mass, phase, tol):
+    import torch
+
+    x = torch.zeros_like(b)
+    solve_overlap(ctx, b, x, mass, tol=tol, phase=[phase] * b.shape[0])
+    return x
+
+
+def correlator_jacobian(ctx: Context, sources, E, charge, mass, tol=1e-12):
+    """dC(t)/dE at field E by the tangent of the solve: dS = -D^-1 (dD/dphi) S q,
+    dC(t) = 2 Re sum <S, dS>_t.  Returns (C, dC/dE) as numpy arrays [Lt]."""
+    import torch
+
+    phase = charge * float(E)
+    S = _solve_columns(ctx, sources, mass, phase, tol)
+    C = correlator(ctx, S)
+    dDS = torch.empty_like(S)
+    apply_dDdphi(ctx, S, dDS, mass, phase=[phase] * S.shape[0])
+    dS = _solve_columns(ctx, dDS, mass, phase, tol)  # D^-1 dD S
+    ip = inner(ctx, S, dS, per_timeslice=True)
+    return C, -2.0 * charge * np.real(ip).sum(axis=0)
+
+
+def _make_correlator_function():
+    import torch
+
+    class PionCorrelator(torch.autograd.Function):
+        """C(t; E) of the point-source propagators at field E, phase phi = charge * E.
+
+        forward: one solve per source and the correlator.  backward: the adjoint solve
+        lam = D^-+ (g o S) = gamma5 D^-1 gamma5 (g o S) and dL/dE = -2 charge Re sum <lam, dD/dphi S>.
+        """
+
+        @staticmethod
+        def forward(fctx, E, ctx, sources, charge, mass, tol):
+            phase = charge * float(E)
+            S = _solve_columns(ctx, sources, mass, phase, tol)
+            fctx.ovl = (ctx, S, charge, mass, tol, phase)
+            return torch.from_numpy(correlator(ctx, S)).to(E.dtype)
+
+        @staticmethod
+        def backward(fctx, gC):
+            ctx, S, charge, mass, tol, phase = fctx.ovl
+            g = gC.detach().cpu().double().numpy()
+            w = torch.empty_like(S)
+            timeslice_scale(ctx, S, w, g, gamma5=True)        # gamma5 (g o S)
+            y = _solve_columns(ctx, w, mass, phase, tol)
+            lam = torch.empty_like(S)
+            timeslice_scale(ctx, y, lam, np.ones(ctx.dims[3]), gamma5=True)
+            dDS = torch.empty_like(S)
+            apply_dDdphi(ctx, S, dDS, mass, phase=[phase] * S.shape[0])
+            ip = inner(ctx, lam, dDS)
+            gE = -2.0 * charge * float(np.real(ip).sum())
+            return torch.tensor(gE, dtype=gC.dtype), None, None, None, None, None
+
+    return PionCorrelator
+
+
+_PION = None
+
+
+def pion_correlator(E, ctx: Context, sources, charge, mass, tol=1e-12):
+    """Differentiable C(t; E) (torch.autograd): E is a 0-d float64 tensor."""
+    global _PION
+    if _PION is None:
+        _PION = _make_correlator_function()
+    return _PION.apply(E, ctx, sources, charge, mass, tol)

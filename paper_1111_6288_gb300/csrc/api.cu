@@ -36,6 +36,11 @@ struct Bank {
     void* V32 = nullptr;  // [n][12][V] float2
     double* d_signs = nullptr;  // [n]
     std::vector<double> signs;
+    std::vector<double> theta;  // eigenvalues of Q
+    // derivative data with respect to the field phase (built on first use)
+    bool dready = false;
+    void* Uh64 = nullptr;           // [n][12][V] double2: low-high vectors u_i
+    std::vector<double2> M;         // [n][n] low-low block F[l_i, l_j] (V^+ dH V)_ij, row-major
 };
 
 struct Buf {
@@ -50,6 +55,7 @@ struct ov_ctx {
     ov_params p;
     std::vector<double> coeffs;
     double hw_norm = 0.0;
+    double delta = 0.0;  // max over [eps, 1] of |1 - sqrt(x) P(x)| (Sec. 2, eq. 2)
     std::string err;
     std::string info;  // summary of the last eigensolver / solve call
     void* U64 = nullptr;
@@ -529,10 +535,20 @@ int register_bank_internal(ov_ctx* c, double phase, const void* W64, int n, cons
         b->V64 = b->V32 = nullptr;
         b->d_signs = nullptr;
     }
+    if (b->Uh64) {
+        CK(cudaFree(b->Uh64));
+        b->Uh64 = nullptr;
+    }
+    b->dready = false;
+    b->M.clear();
     b->n = n;
     b->signs.assign(n, 1.0);
+    b->theta.assign(n, 0.0);
     if (n == 0) return OV_OK;
-    for (int i = 0; i < n; ++i) b->signs[i] = (lam[i] >= 0.0) ? 1.0 : -1.0;
+    for (int i = 0; i < n; ++i) {
+        b->signs[i] = (lam[i] >= 0.0) ? 1.0 : -1.0;
+        b->theta[i] = lam[i];
+    }
     const size_t b64 = vec_bytes(c, OV_PREC_F64) * n, b32 = vec_bytes(c, OV_PREC_F32) * n;
     if (cudaMalloc(&b->V64, b64) != cudaSuccess || cudaMalloc(&b->V32, b32) != cudaSuccess ||
         cudaMalloc(&b->d_signs, sizeof(double) * n) != cudaSuccess) {
@@ -643,6 +659,24 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     else host_chebyshev_coeffs(p->poly_degree, p->eps, c->coeffs.data());
     c->p.coeffs = nullptr;
     c->hw_norm = p->hw_norm > 0.0 ? p->hw_norm : std::fabs(4.0 + p->m0) + 4.0;
+    {
+        // delta of the polynomial on a grid uniform in the Chebyshev angle (Clenshaw in FP64)
+        const int ng = 4096, n = p->poly_degree;
+        double worst = 0.0;
+        for (int q = 0; q <= ng; ++q) {
+            const double y = std::cos(3.141592653589793 * q / ng);
+            double b1 = 0.0, b2 = 0.0;
+            for (int k = n; k >= 1; --k) {
+                const double b0 = c->coeffs[k] + 2.0 * y * b1 - b2;
+                b2 = b1;
+                b1 = b0;
+            }
+            const double P = c->coeffs[0] + y * b1 - b2;
+            const double x = ((1.0 - p->eps) * y + 1.0 + p->eps) / 2.0;
+            worst = std::max(worst, std::fabs(1.0 - std::sqrt(x) * P));
+        }
+        c->delta = worst;
+    }
     if (c->p.max_iter <= 0) c->p.max_iter = 100000;
     *out = c;
     return OV_OK;
@@ -657,6 +691,7 @@ int ov_destroy(ov_ctx* c) {
         if (b.V64) cudaFree(b.V64);
         if (b.V32) cudaFree(b.V32);
         if (b.d_signs) cudaFree(b.d_signs);
+        if (b.Uh64) cudaFree(b.Uh64);
     }
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -679,6 +714,8 @@ const char* ov_last_info(const ov_ctx* c) { return c ? c->info.c_str() : ""; }
 long long ov_volume(const ov_ctx* c) { return c ? c->g.V : 0; }
 
 double ov_hw_norm(const ov_ctx* c) { return c ? c->hw_norm : 0.0; }
+
+double ov_poly_delta(const ov_ctx* c) { return c ? c->delta : 0.0; }
 
 int ov_chebyshev_coeffs(int n, double eps, double* out) {
     if (n < 0 || !out || !(eps > 0.0 && eps < 1.0)) return OV_ERR_ARG;
@@ -1209,3 +1246,411 @@ extern "C" int solve_overlap(ov_ctx* c, double mass, const double* phase, const 
     return c->p.inner_precision == OV_PREC_F64 ? solve_impl<double>(c, mass, S, b, x, tol, stats, s)
                                                : solve_impl<float>(c, mass, S, b, x, tol, stats, s);
 }
+
+// ============================================================================
+// Derivatives with respect to the field phase phi = q E (background-field method,
+// Sec. 4).  The implemented sign function is F(H) = sum_{low} sign(l_i) P_i +
+// sum_{high} q(l_i) P_i; its exact derivative along dH = dH_w/dphi is the
+// Daleckii-Krein sum dF = sum_ij F[l_i, l_j] P_i dH P_j, taken here in three blocks:
+//   high-high  Pi_perp (dq(H)[dH]) Pi_perp: the tangent of the Clenshaw recurrence
+//              (recomputed alongside it, nothing stored);
+//   low-low    V M V^+, M_ij = (s_i - s_j)/(l_i - l_j) (V^+ dH V)_ij;
+//   low-high   sum_i v_i <u_i, .> + u_i <v_i, .>, u_i = sum_{high j} F[l_i, l_j] P_j dH v_i.
+// In the low-high block F[l_i, l_j] = (s_i - q(l_j))/(l_i - l_j) is taken with sign(l_j)
+// for q(l_j): the two differ by the polynomial error delta.  Then only pairs of opposite
+// sign remain, F = 2/(h(|t_i| + |t_j|)) in units of Q (t = l/h), and
+// u_i = (2/h) rho_i(Q^2) Pi_perp (1 - s_i sign)/2 dH v_i with rho_i(x) = 1/(|t_i| + sqrt(x)),
+// a Chebyshev polynomial per mode on the interval of the sign function.
+// ============================================================================
+
+namespace {
+
+// Y_r = P_r(Q^2) X_r for per-system polynomials P_r = sum_k coef[r][k] T_k(Y), Y = (2 Q^2 -
+// (1 + eps))/(1 - eps) on the context's interval [eps, 1] (FP64, same Clenshaw recurrence as
+// the sign function; coef: device [ns][n+1]).
+int poly_per_system(ov_ctx* c, const void* X, const SysSet& S, const double* d_coef, void* Yout, cudaStream_t s) {
+    const int ns = S.n;
+    const long long n12 = 12LL * c->g.V;
+    void *bA, *bB, *t;
+    TRY(workspace(c, "pp_bA", OV_PREC_F64, ns, &bA));
+    TRY(workspace(c, "pp_bB", OV_PREC_F64, ns, &bB));
+    TRY(workspace(c, "pp_t", OV_PREC_F64, ns, &t));
+    TRY(upload_sys(c, S, s));
+    const double* d_phase = any_phase(S) ? c->d_phase : nullptr;
+    const int n = c->p.poly_degree;
+    const double eps = c->p.eps, h = c->hw_norm, m0 = c->p.m0;
+    const double alpha = 4.0 / ((1.0 - eps) * h * h);
+    const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
+    // b_n = c_n x: an epilogue-only pass (c_op = 0) that scales per system
+    Epilogue e0;
+    e0.c_op = 0.0;
+    e0.c2 = 1.0;
+    e0.v2 = X;
+    e0.c2r = d_coef + n;
+    e0.c2r_stride = n + 1;
+    launch_dslash<double>(c->g, m0, c->U64, X, bA, ns, d_phase, e0, s);
+    void *b1 = bA, *b2 = nullptr;
+    Epilogue plain;
+    for (int k = n - 1; k >= 0; --k) {
+        const double hf = (k == 0) ? 0.5 : 1.0;
+        launch_dslash<double>(c->g, m0, c->U64, b1, t, ns, d_phase, plain, s);
+        Epilogue e;
+        e.c_op = alpha * hf;
+        e.c1 = beta * hf;
+        e.v1 = b1;
+        e.c2 = 1.0;
+        e.v2 = X;
+        e.c2r = d_coef + k;
+        e.c2r_stride = n + 1;
+        e.c3 = -1.0;
+        e.v3 = b2;
+        void* o = (k == 0) ? Yout : (b2 ? b2 : bB);
+        launch_dslash<double>(c->g, m0, c->U64, t, o, ns, d_phase, e, s);
+        b2 = b1;
+        b1 = o;
+    }
+    CKL();
+    c->dslash_count += (2LL * n + 1) * ns;
+    return OV_OK;
+}
+
+// Small dense helpers on device matrices through the host (n x k, row-major double2).
+int download(ov_ctx* c, const double2* d, size_t n, std::vector<double2>& h, cudaStream_t s) {
+    h.resize(n);
+    CK(cudaMemcpyAsync(h.data(), d, sizeof(double2) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return OV_OK;
+}
+
+// out_j = alpha X_j + sum_i A_i C[i][j] with C given on the host ([na][nb], row-major).
+int combine_host(ov_ctx* c, const void* A, int na, const std::vector<double2>& C, int nb, double alpha, const void* X,
+                 void* out, cudaStream_t s) {
+    const long long n12 = 12LL * c->g.V;
+    TRY(ensure_small(c, (long long)na * nb, 0, 1));
+    CK(cudaMemcpyAsync(c->d_C, C.data(), sizeof(double2) * na * nb, cudaMemcpyHostToDevice, s));
+    combine<double>(A, n12, na, c->d_C, nb, nb, alpha, X, n12, out, n12, n12, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));  // d_C is reused by the next call
+    return OV_OK;
+}
+
+// V^+ X for na bank vectors and nb vectors, to the host ([na][nb], row-major).
+int vdotx(ov_ctx* c, const void* A, int na, const void* X, int nb, std::vector<double2>& out, cudaStream_t s) {
+    const long long n12 = 12LL * c->g.V;
+    TRY(ensure_small(c, (long long)na * nb, (long long)na * nb * 4 * 152, 1));
+    multidot<double>(A, n12, na, X, n12, nb, n12, c->d_C, c->d_partial, c->partial_cap, s);
+    CKL();
+    return download(c, c->d_C, (size_t)na * nb, out, s);
+}
+
+// Low-low matrix M and low-high vectors u_i of a bank (FP64).
+int prepare_bank_derivative(ov_ctx* c, Bank* b, cudaStream_t s) {
+    if (b->dready || b->n == 0) {
+        b->dready = true;
+        return OV_OK;
+    }
+    const int N = b->n;
+    const double h = c->hw_norm;
+    const long long n12 = 12LL * c->g.V;
+    const size_t vb = vec_bytes(c, OV_PREC_F64);
+    void *dV, *SdV, *Z;
+    TRY(workspace(c, "dv_dV", OV_PREC_F64, N, &dV));
+    TRY(workspace(c, "dv_SdV", OV_PREC_F64, N, &SdV));
+    TRY(workspace(c, "dv_Z", OV_PREC_F64, N, &Z));
+    SysSet S;
+    S.n = N;
+    S.phase.assign(N, b->phase);
+    TRY(upload_sys(c, S, s));
+    Epilogue plain;
+    launch_dslash<double>(c->g, c->p.m0, c->U64, b->V64, dV, N, c->d_phase, plain, s, true);  // dH v_i
+    CKL();
+    // low-low: M_ij = (s_i - s_j)/(h (t_i - t_j)) K_ij,  K = V^+ dH V
+    std::vector<double2> K;
+    TRY(vdotx(c, b->V64, N, dV, N, K, s));
+    b->M.assign((size_t)N * N, make_double2(0, 0));
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            if (b->signs[i] == b->signs[j]) continue;
+            const double f = (b->signs[i] - b->signs[j]) / (h * (b->theta[i] - b->theta[j]));
+            b->M[(size_t)i * N + j] = make_double2(f * K[(size_t)i * N + j].x, f * K[(size_t)i * N + j].y);
+        }
+    // y_i = Pi_perp (1 - s_i sign)/2 dH v_i
+    Epilogue fin;
+    fin.c_op = 1.0 / h;
+    fin.c1 = 1.0;
+    TRY(sign_pipeline<double>(c, dV, S, false, fin, SdV, s));
+    std::vector<double> a(N), half(N, 0.5);
+    for (int i = 0; i < N; ++i) a[i] = -0.5 * b->signs[i];
+    launch_axpby<double>(a.data(), SdV, half.data(), dV, n12, N, s);
+    CKL();
+    std::vector<double2> C;
+    TRY(vdotx(c, b->V64, N, dV, N, C, s));
+    for (auto& v : C) v = make_double2(-v.x, -v.y);
+    TRY(combine_host(c, b->V64, N, C, N, 1.0, dV, SdV, s));  // SdV <- Pi_perp y
+    // z_i = rho_i(Q^2) y_i, rho_i(x) = 1/(|t_i| + sqrt(x)): on the opposite-sign part
+    // (|t_i| + |Q|)^{-1} = (|t_i| - s_i Q)^{-1}, and bounded on every other part of the large space
+    const int n = c->p.poly_degree;
+    std::vector<double> coef((size_t)N * (n + 1));
+    for (int i = 0; i < N; ++i)
+        host_chebyshev_coeffs_shifted_inverse_root(n, c->p.eps, std::fabs(b->theta[i]), &coef[(size_t)i * (n + 1)]);
+    double* d_coef = nullptr;
+    if (cudaMalloc(&d_coef, sizeof(double) * coef.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "allocation of per-mode coefficients failed");
+    }
+    CK(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s));
+    const int rc = poly_per_system(c, SdV, S, d_coef, Z, s);
+    CK(cudaStreamSynchronize(s));
+    cudaFree(d_coef);
+    TRY(rc);
+    if (cudaMalloc(&b->Uh64, vb * N) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "allocation of the bank derivative vectors failed");
+    }
+    launch_scale<double>(2.0 / h, Z, b->Uh64, n12 * N, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    b->dready = true;
+    return OV_OK;
+}
+
+// Y = dq(H)[dH] X for the polynomial part q(H) = Q P(Q^2) (no projection), FP64: the tangent
+// of the Clenshaw recurrence b_k = c_k x + 2 Y b_{k+1} - b_{k+2} with x fixed:
+//   db_k = 2 dY b_{k+1} + 2 Y db_{k+1} - db_{k+2},  2 dY = alpha (dH H + H dH),
+// and d(Q p) = (dH p + H dp)/h.
+int tangent_poly(ov_ctx* c, const void* X, const SysSet& S, void* Y, cudaStream_t s) {
+    const int ns = S.n;
+    const long long n12 = 12LL * c->g.V;
+    const size_t vb = vec_bytes(c, OV_PREC_F64);
+    void *bA, *bB, *dA, *dB, *t, *u, *sv, *r;
+    TRY(workspace(c, "tg_bA", OV_PREC_F64, ns, &bA));
+    TRY(workspace(c, "tg_bB", OV_PREC_F64, ns, &bB));
+    TRY(workspace(c, "tg_dA", OV_PREC_F64, ns, &dA));
+    TRY(workspace(c, "tg_dB", OV_PREC_F64, ns, &dB));
+    TRY(workspace(c, "tg_t", OV_PREC_F64, ns, &t));
+    TRY(workspace(c, "tg_u", OV_PREC_F64, ns, &u));
+    TRY(workspace(c, "tg_s", OV_PREC_F64, ns, &sv));
+    TRY(workspace(c, "tg_r", OV_PREC_F64, ns, &r));
+    TRY(upload_sys(c, S, s));
+    const double* d_phase = any_phase(S) ? c->d_phase : nullptr;
+    const int n = c->p.poly_degree;
+    const double eps = c->p.eps, h = c->hw_norm, m0 = c->p.m0;
+    const double alpha = 4.0 / ((1.0 - eps) * h * h);
+    const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
+    const void* U = c->U64;
+    launch_scale<double>(c->coeffs[n], X, bA, ns * n12, s);
+    CK(cudaMemsetAsync(dA, 0, vb * ns, s));
+    void *b1 = bA, *b2 = nullptr, *db1 = dA, *db2 = nullptr;
+    Epilogue plain, derv;
+    for (int k = n - 1; k >= 0; --k) {
+        const double hf = (k == 0) ? 0.5 : 1.0;
+        launch_dslash<double>(c->g, m0, U, b1, t, ns, d_phase, plain, s);          // t = H b1
+        launch_dslash<double>(c->g, m0, U, b1, u, ns, d_phase, derv, s, true);     // u = dH b1
+        Epilogue es;
+        es.c1 = 1.0;
+        es.v1 = u;
+        launch_dslash<double>(c->g, m0, U, db1, sv, ns, d_phase, es, s);           // s = H db1 + u
+        launch_dslash<double>(c->g, m0, U, t, r, ns, d_phase, derv, s, true);      // r = dH t
+        Epilogue eb;
+        eb.c_op = alpha * hf;
+        eb.c1 = beta * hf;
+        eb.v1 = b1;
+        eb.c2 = c->coeffs[k];
+        eb.v2 = X;
+        eb.c3 = -1.0;
+        eb.v3 = b2;
+        void* ob = b2 ? b2 : bB;
+        launch_dslash<double>(c->g, m0, U, t, ob, ns, d_phase, eb, s);             // b_k
+        Epilogue ed;
+        ed.c_op = alpha * hf;
+        ed.c1 = beta * hf;
+        ed.v1 = db1;
+        ed.c2 = alpha * hf;
+        ed.v2 = r;
+        ed.c3 = -1.0;
+        ed.v3 = db2;
+        void* od = db2 ? db2 : dB;
+        launch_dslash<double>(c->g, m0, U, sv, od, ns, d_phase, ed, s);            // db_k
+        b2 = b1;
+        b1 = ob;
+        db2 = db1;
+        db1 = od;
+    }
+    CKL();
+    c->dslash_count += 6LL * n * ns;
+    // Y = (H dp + dH p)/h with p = b1, dp = db1
+    Epilogue ep;
+    ep.c_op = 1.0 / h;
+    launch_dslash<double>(c->g, m0, U, b1, t, ns, d_phase, ep, s, true);           // t = dH p / h
+    Epilogue ey;
+    ey.c_op = 1.0 / h;
+    ey.c1 = 1.0;
+    ey.v1 = t;
+    launch_dslash<double>(c->g, m0, U, db1, Y, ns, d_phase, ey, s);
+    CKL();
+    return OV_OK;
+}
+
+// out = d sign(H_w)/dphi X (FP64 internal vectors), per run of equal phase.
+int dsign_dphi(ov_ctx* c, const void* X, const SysSet& Sall, void* out, cudaStream_t s) {
+    const long long n12 = 12LL * c->g.V;
+    const size_t vb = vec_bytes(c, OV_PREC_F64);
+    void *Xp, *Yt, *T1;
+    TRY(workspace(c, "ds_Xp", OV_PREC_F64, Sall.n, &Xp));
+    TRY(workspace(c, "ds_Y", OV_PREC_F64, Sall.n, &Yt));
+    TRY(workspace(c, "ds_T", OV_PREC_F64, Sall.n, &T1));
+    for (int j0 = 0; j0 < Sall.n;) {
+        int j1 = j0 + 1;
+        while (j1 < Sall.n && Sall.phase[j1] == Sall.phase[j0]) ++j1;
+        const int k = j1 - j0;
+        SysSet S;
+        S.n = k;
+        S.phase.assign(k, Sall.phase[j0]);
+        const char* Xj = (const char*)X + (size_t)j0 * vb;
+        char* Oj = (char*)out + (size_t)j0 * vb;
+        Bank* b = find_bank(c, Sall.phase[j0]);
+        if (!b && Sall.phase[j0] != 0.0)
+            return fail(c, OV_ERR_NO_BANK, "no small-space bank registered for phase %.17g", Sall.phase[j0]);
+        const int N = b ? b->n : 0;
+        std::vector<double2> Cv, Du, E;
+        if (N > 0) {
+            TRY(prepare_bank_derivative(c, b, s));
+            TRY(vdotx(c, b->V64, N, Xj, k, Cv, s));   // V^+ X
+            TRY(vdotx(c, b->Uh64, N, Xj, k, Du, s));  // U^+ X
+            std::vector<double2> Cn(Cv.size());
+            for (size_t q = 0; q < Cv.size(); ++q) Cn[q] = make_double2(-Cv[q].x, -Cv[q].y);
+            TRY(combine_host(c, b->V64, N, Cn, k, 1.0, Xj, Xp, s));  // Xp = X - V V^+ X
+        } else {
+            CK(cudaMemcpyAsync(Xp, Xj, vb * k, cudaMemcpyDeviceToDevice, s));
+        }
+        TRY(tangent_poly(c, Xp, S, Yt, s));
+        if (N > 0) {
+            TRY(vdotx(c, b->V64, N, Yt, k, E, s));
+            // C1 = -V^+ Y + M V^+ X + U^+ X   ([N][k])
+            std::vector<double2> C1((size_t)N * k);
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < k; ++j) {
+                    double re = -E[(size_t)i * k + j].x + Du[(size_t)i * k + j].x;
+                    double im = -E[(size_t)i * k + j].y + Du[(size_t)i * k + j].y;
+                    for (int l = 0; l < N; ++l) {
+                        const double2 m = b->M[(size_t)i * N + l], x = Cv[(size_t)l * k + j];
+                        re += m.x * x.x - m.y * x.y;
+                        im += m.x * x.y + m.y * x.x;
+                    }
+                    C1[(size_t)i * k + j] = make_double2(re, im);
+                }
+            TRY(combine_host(c, b->V64, N, C1, k, 1.0, Yt, T1, s));  // T1 = Y + V C1
+            TRY(combine_host(c, b->Uh64, N, Cv, k, 1.0, T1, Oj, s));  // out = T1 + U V^+ X
+        } else {
+            CK(cudaMemcpyAsync(Oj, Yt, vb * k, cudaMemcpyDeviceToDevice, s));
+        }
+        j0 = j1;
+    }
+    return OV_OK;
+}
+
+__global__ void timeslice_scale_k(const double2* __restrict__ in, double2* __restrict__ out, const double* __restrict__ w,
+                                  long long seg, int Lt, long long total, int g5) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)((i / seg) % Lt);
+        const int comp = (int)(i % 12);
+        double f = w[t];
+        if (g5 && comp >= 6) f = -f;
+        const double2 v = in[i];
+        out[i] = make_double2(f * v.x, f * v.y);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ov_apply_dHdphi(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, ov_stream_t stream) {
+    TRY(check_ready(c, in, out, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    void *X, *Y;
+    TRY(workspace(c, "io_in", OV_PREC_F64, nrhs, &X));
+    TRY(workspace(c, "io_out", OV_PREC_F64, nrhs, &Y));
+    launch_pack_spinor<double>(in, OV_C128, X, c->g.V, nrhs, s);
+    SysSet S = make_sys(nrhs, phase);
+    TRY(phase_check(c, S));
+    TRY(upload_sys(c, S, s));
+    Epilogue e;
+    launch_dslash<double>(c->g, c->p.m0, c->U64, X, Y, nrhs, c->d_phase, e, s, true);
+    launch_unpack_spinor<double>(Y, out, OV_C128, c->g.V, nrhs, s);
+    CKL();
+    return OV_OK;
+}
+
+int ov_apply_dDdphi(ov_ctx* c, const void* in, void* out, int nrhs, double mass, const double* phase,
+                    ov_stream_t stream) {
+    TRY(check_ready(c, in, out, nrhs));
+    if (!std::isfinite(mass)) return fail(c, OV_ERR_ARG, "mass not finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *X, *Y;
+    TRY(workspace(c, "dd_in", OV_PREC_F64, nrhs, &X));
+    TRY(workspace(c, "dd_out", OV_PREC_F64, nrhs, &Y));
+    launch_pack_spinor<double>(in, OV_C128, X, c->g.V, nrhs, s);
+    CKL();
+    SysSet S = make_sys(nrhs, phase);
+    TRY(phase_check(c, S));
+    TRY(dsign_dphi(c, X, S, Y, s));
+    // dD(m)/dphi = (1 - m/2) gamma5 dsign/dphi
+    launch_gamma5<double>(Y, X, c->g.V, nrhs, s);
+    launch_scale<double>(1.0 - 0.5 * mass, X, Y, 12LL * c->g.V * nrhs, s);
+    launch_unpack_spinor<double>(Y, out, OV_C128, c->g.V, nrhs, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    return OV_OK;
+}
+
+int ov_correlator(ov_ctx* c, const void* S, int nrhs, double* C, ov_stream_t stream) {
+    if (!c || !S || !C || nrhs < 1) return c ? fail(c, OV_ERR_ARG, "invalid correlator arguments") : OV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Lt = c->g.L[3];
+    const long long seg = 12LL * (c->g.V / Lt);  // complex numbers per (rhs, timeslice)
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * nrhs * Lt, nrhs * Lt));
+    std::vector<double> n2((size_t)nrhs * Lt);
+    norm2_rhs<double>(S, seg, nrhs * Lt, n2.data(), c->d_partial, c->d_red, s);
+    CKL();
+    for (int t = 0; t < Lt; ++t) {
+        double acc = 0.0;
+        for (int j = 0; j < nrhs; ++j) acc += n2[(size_t)j * Lt + t];
+        C[t] = acc;
+    }
+    return OV_OK;
+}
+
+int ov_timeslice_scale(ov_ctx* c, const void* in, void* out, int nrhs, const double* w, int gamma5,
+                       ov_stream_t stream) {
+    if (!c || !in || !out || !w || nrhs < 1) return c ? fail(c, OV_ERR_ARG, "invalid arguments") : OV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Lt = c->g.L[3];
+    TRY(ensure_small(c, (Lt + 1) / 2 + 1, 0, 1));
+    double* d_w = (double*)c->d_C2;
+    CK(cudaMemcpyAsync(d_w, w, sizeof(double) * Lt, cudaMemcpyHostToDevice, s));
+    const long long seg = 12LL * (c->g.V / Lt), total = 12LL * c->g.V * nrhs;
+    timeslice_scale_k<<<152 * 8, 256, 0, s>>>((const double2*)in, (double2*)out, d_w, seg, Lt, total, gamma5);
+    count_launch();
+    CKL();
+    CK(cudaStreamSynchronize(s));  // d_w is reused
+    return OV_OK;
+}
+
+int ov_inner(ov_ctx* c, const void* a, const void* b, int nrhs, int per_timeslice, double* out, ov_stream_t stream) {
+    if (!c || !a || !b || !out || nrhs < 1) return c ? fail(c, OV_ERR_ARG, "invalid arguments") : OV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nseg = per_timeslice ? nrhs * c->g.L[3] : nrhs;
+    const long long seg = per_timeslice ? 12LL * (c->g.V / c->g.L[3]) : 12LL * c->g.V;
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * nseg, nseg));
+    std::vector<double2> r(nseg);
+    dot_rhs<double>(a, b, seg, nseg, r.data(), c->d_partial, c->d_red, s);
+    CKL();
+    for (int j = 0; j < nseg; ++j) {
+        out[2 * j] = r[j].x;
+        out[2 * j + 1] = r[j].y;
+    }
+    return OV_OK;
+}
+
+}  // extern "C"

@@ -165,6 +165,8 @@ struct Args {
     const void* v3;
     const double* phase;
     const signed char* chi;
+    const double* c2r;
+    long long c2r_stride;
     R c_op, c1, c2, c3, diag;
     R bcf[4];
     int L[4];
@@ -260,7 +262,11 @@ __device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int 
 
 constexpr int DSLASH_THREADS = OVL_DSLASH_THREADS;
 
-template <typename R>
+// DERIV: instead of H_w, its derivative with respect to the field phase phi of the
+// right-hand side: only the x hops depend on phi, through exp(i phi t) U_x(n) (forward)
+// and exp(-i phi t) U_x(n-x)^+ (backward), whose derivatives bring the factors i t and
+// -i t; the mass term drops out.
+template <typename R, bool DERIV>
 __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_kernel(Args<R> a, int nrhs) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
@@ -282,27 +288,40 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
         sincos(a.phase[r] * (double)x3, &sn, &cs);
         ph = {(R)cs, (R)sn};
     }
+    const R cop = a.c_op, c1 = a.c1;
+    const R c2 = a.c2r ? a.c2 * (R)a.c2r[(long long)r * a.c2r_stride] : a.c2;
     Cx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-    both_hops<R, 0>(a, in, s, x0, ph, acc);
-    both_hops<R, 1>(a, in, s, x1, ph, acc);
-    both_hops<R, 2>(a, in, s, x2, ph, acc);
-    both_hops<R, 3>(a, in, s, x3, ph, acc);
-
-    // z = c_op * gamma5 (diag psi - acc/2) + c1 v1
     Cx<R> z[12], tmp[12];
-    IO<R>::load(in, V, s, tmp);
+    if constexpr (DERIV) {
+        const R tt = (R)x3;
+        both_hops<R, 0>(a, in, s, x0, {-tt * ph.im, tt * ph.re}, acc);  // i t exp(i phi t)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        Cx<R> d = csub(cscale(a.diag, tmp[k]), cscale(R(0.5), acc[k]));
-        if (k >= 6) d = {-d.re, -d.im};  // gamma5
-        z[k] = cscale(a.c_op, d);
+        for (int k = 0; k < 12; ++k) {
+            Cx<R> d = cscale(R(-0.5), acc[k]);
+            if (k >= 6) d = {-d.re, -d.im};  // gamma5
+            z[k] = cscale(cop, d);
+        }
+    } else {
+        both_hops<R, 0>(a, in, s, x0, ph, acc);
+        both_hops<R, 1>(a, in, s, x1, ph, acc);
+        both_hops<R, 2>(a, in, s, x2, ph, acc);
+        both_hops<R, 3>(a, in, s, x3, ph, acc);
+        // z = c_op * gamma5 (diag psi - acc/2)
+        IO<R>::load(in, V, s, tmp);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            Cx<R> d = csub(cscale(a.diag, tmp[k]), cscale(R(0.5), acc[k]));
+            if (k >= 6) d = {-d.re, -d.im};  // gamma5
+            z[k] = cscale(cop, d);
+        }
     }
+    // + c1 v1
     if (a.v1) {
         IO<R>::load((const char*)a.v1 + off, V, s, tmp);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c1, tmp[k]));
+        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(c1, tmp[k]));
     }
     if (a.g5) {
 #pragma unroll
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
     if (a.v2) {
         IO<R>::load((const char*)a.v2 + off, V, s, tmp);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c2, tmp[k]));
+        for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(c2, tmp[k]));
     }
     if (a.v3) {
         // v3 may alias out: plain loads; the same thread reads then writes site s
@@ -338,7 +357,7 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
 
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
-                   const double* d_phase, const Epilogue& e, cudaStream_t s) {
+                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv) {
     Args<R> a;
     a.U = links;
     a.in = in;
@@ -348,6 +367,8 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
     a.v3 = e.v3;
     a.phase = d_phase;
     a.chi = e.chi;
+    a.c2r = e.c2r;
+    a.c2r_stride = e.c2r_stride;
     a.c_op = (R)e.c_op;
     a.c1 = (R)e.c1;
     a.c2 = (R)e.c2;
@@ -365,13 +386,14 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
     const int by = nrhs > 1 ? 2 : 1, bx = DSLASH_THREADS / by;
     dim3 block(bx, by);
     dim3 grid((g.V + bx - 1) / bx, (nrhs + by - 1) / by);
-    dslash_kernel<R><<<grid, block, 0, s>>>(a, nrhs);
+    if (deriv) dslash_kernel<R, true><<<grid, block, 0, s>>>(a, nrhs);
+    else dslash_kernel<R, false><<<grid, block, 0, s>>>(a, nrhs);
     count_launch();
 }
 
 template void launch_dslash<double>(const Geom&, double, const void*, const void*, void*, int, const double*,
-                                    const Epilogue&, cudaStream_t);
+                                    const Epilogue&, cudaStream_t, bool);
 template void launch_dslash<float>(const Geom&, double, const void*, const void*, void*, int, const double*,
-                                   const Epilogue&, cudaStream_t);
+                                   const Epilogue&, cudaStream_t, bool);
 
 }  // namespace ovl

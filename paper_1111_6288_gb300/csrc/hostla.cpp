@@ -121,22 +121,32 @@ void host_eigh(int n, std::vector<HostCplx>& Ain, std::vector<double>& w, std::v
     for (size_t k = 0; k < A.size(); ++k) Ain[k] = HostCplx{A[k].real(), A[k].imag()};
 }
 
-void host_chebyshev_coeffs(int n, double eps, double* out) {
-    // Interpolation at the Chebyshev-Gauss nodes y_j = cos(theta_j), theta_j = pi (j + 1/2)/(n + 1),
-    // mapped to x_j = ((1 - eps) y_j + 1 + eps)/2 in [eps, 1]; f(x) = x^{-1/2}.
+namespace {
+// Interpolation at the Chebyshev-Gauss nodes y_j = cos(theta_j), theta_j = pi (j + 1/2)/(n + 1),
+// mapped to x_j = ((1 - eps) y_j + 1 + eps)/2 in [eps, 1].
+template <typename F>
+void cheb_interp(int n, double eps, F f, double* out) {
     const double pi = std::acos(-1.0);
-    std::vector<double> f(n + 1), th(n + 1);
+    std::vector<double> fv(n + 1), th(n + 1);
     for (int j = 0; j <= n; ++j) {
         th[j] = pi * (j + 0.5) / (n + 1);
-        const double x = ((1.0 - eps) * std::cos(th[j]) + 1.0 + eps) / 2.0;
-        f[j] = 1.0 / std::sqrt(x);
+        fv[j] = f(((1.0 - eps) * std::cos(th[j]) + 1.0 + eps) / 2.0);
     }
     for (int k = 0; k <= n; ++k) {
         double s = 0.0;
-        for (int j = 0; j <= n; ++j) s += f[j] * std::cos(k * th[j]);
+        for (int j = 0; j <= n; ++j) s += fv[j] * std::cos(k * th[j]);
         out[k] = 2.0 * s / (n + 1);
     }
     out[0] *= 0.5;
+}
+}  // namespace
+
+void host_chebyshev_coeffs(int n, double eps, double* out) {
+    cheb_interp(n, eps, [](double x) { return 1.0 / std::sqrt(x); }, out);
+}
+
+void host_chebyshev_coeffs_shifted_inverse_root(int n, double eps, double a, double* out) {
+    cheb_interp(n, eps, [a](double x) { return 1.0 / (a + std::sqrt(x)); }, out);
 }
 
 }  // namespace ovl

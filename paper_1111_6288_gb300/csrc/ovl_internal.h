@@ -49,12 +49,16 @@ struct Epilogue {
     const void* v3 = nullptr;
     int g5 = 0;
     const signed char* chi = nullptr;  // device [nrhs]
+    const double* c2r = nullptr;       // device: c2 of rhs j is c2 * c2r[j * c2r_stride] if set
+    long long c2r_stride = 0;
 };
 
 // ---- kernels: dslash.cu ---------------------------------------------------
+// deriv: apply dH_w/dphi (the phi-derivative of the x hops, per right-hand-side phase) in
+// place of H_w; the epilogue is the same.
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
-                   const double* d_phase, const Epilogue& e, cudaStream_t s);
+                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv = false);
 
 // ---- kernels: blas.cu -----------------------------------------------------
 // ABI spinor [rhs][site][12] (dtype_in: 0 complex128, 1 complex64) -> internal [rhs][12][V] of R.
@@ -133,5 +137,7 @@ void host_inv_lower_dag(int n, const std::vector<HostCplx>& L, std::vector<HostC
 void host_eigh(int n, std::vector<HostCplx>& A, std::vector<double>& w, std::vector<HostCplx>& Z);
 // Chebyshev interpolant coefficients of x^{-1/2} on [eps, 1] (c_0 halved).
 void host_chebyshev_coeffs(int n, double eps, double* out);
+// The same for 1/(a + sqrt(x)), a > 0.
+void host_chebyshev_coeffs_shifted_inverse_root(int n, double eps, double a, double* out);
 
 }  // namespace ovl

@@ -94,3 +94,11 @@ def test_create_resolves_norm_bound(ovl):
     assert ctx.volume == 512
     assert ctx.hw_norm == pytest.approx(6.5)
     ctx.close()
+
+
+@pytest.mark.parametrize("n,eps", [(64, 0.01), (527, 4e-4)])
+def test_library_polynomial_delta_matches_oracle(ovl, n, eps):
+    ctx = ovl.Context(ovl.Params(dims=(4, 4, 4, 4), eps=eps, poly_degree=n))
+    want = chebyshev.approximation_error(chebyshev.chebyshev_coeffs(n, eps), eps)
+    assert ctx.delta == pytest.approx(want, rel=0.05)
+    ctx.close()
