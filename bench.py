@@ -411,6 +411,7 @@ def main():
             "time_to_solution": {"mixed_s": mean_mixed_s, "fp64_s": fp64["seconds"] if fp64 else None,
                                  "speedup": (fp64["seconds"] / mean_mixed_s) if fp64 else None,
                                  "mixed_outer_iters": stats[0].outer_iters, "mixed_inner_iters": stats[0].inner_iters,
+                                 "mixed_sign_applies": stats[0].sign_applies,
                                  "mixed_true_residual": worst_res, "fp64": fp64},
             "dov_apply_per_s": {"f32": rate32, "f64": rate64},
             "dslash_gbs": achieved,

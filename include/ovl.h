@@ -92,7 +92,7 @@ typedef struct ov_params {
     int max_nrhs;         /* largest nrhs of any call, >= 1 */
     int max_iter;         /* cap on inner CG iterations per solve (<= 0: 100000) */
     double inner_tol;     /* relative tolerance of each inner solve (<= 0: default,
-                             1e-5 for F32, 0.1 * tol for F64) */
+                             1e-6 for F32; for F64 the outer target itself) */
 } ov_params;
 
 /* Per-solve statistics, filled on the host when solve_overlap returns. */
@@ -128,6 +128,9 @@ int ov_destroy(ov_ctx* ctx);
 const char* ov_last_error(const ov_ctx* ctx);
 /* Human-readable summary of the last eigensolver call on ctx (cycles, residuals, time). */
 const char* ov_last_info(const ov_ctx* ctx);
+/* Timings of the Wilson-kernel right-hand-side blocks the library tried (1, 2 or 4 systems per
+ * thread block) for each batch size it met; the fastest is used from then on. */
+const char* ov_tune_info(const ov_ctx* ctx);
 /* Number of lattice sites. */
 long long ov_volume(const ov_ctx* ctx);
 /* ||H_w|| in use (after the hw_norm <= 0 default is resolved). */

@@ -71,6 +71,7 @@ _SIGNATURES = {
     "ov_destroy": (_I, [_VP]),
     "ov_last_error": (C.c_char_p, [_VP]),
     "ov_last_info": (C.c_char_p, [_VP]),
+    "ov_tune_info": (C.c_char_p, [_VP]),
     "ov_volume": (C.c_longlong, [_VP]),
     "ov_hw_norm": (_D, [_VP]),
     "ov_poly_delta": (_D, [_VP]),
@@ -206,6 +207,11 @@ class Context:
     def last_info(self):
         """Summary of the last eigensolver call on this context."""
         return lib().ov_last_info(self.handle).decode()
+
+    @property
+    def tune_info(self):
+        """Timings of the Wilson-kernel right-hand-side blocks tried so far."""
+        return lib().ov_tune_info(self.handle).decode()
 
     @property
     def volume(self):

@@ -250,9 +250,10 @@ __device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int 
     }
 }
 
-// Block = DSLASH_THREADS threads: all sites x 1 right-hand side, or half the sites x 2
-// right-hand sides when there are several, so that the threads of one site share the
-// SM's L1 for the site's links.  DSLASH_MIN_BLOCKS bounds the registers per thread.
+// Block = DSLASH_THREADS threads = (DSLASH_THREADS / b sites) x (b right-hand sides), b in
+// {1, 2, 4} (the caller's rhs_block, autotuned by the library; default 1 for one
+// right-hand side, else 2), so that the threads of one site share the SM's L1 for the
+// site's links.  DSLASH_MIN_BLOCKS bounds the registers per thread.
 #ifndef OVL_DSLASH_THREADS
 #define OVL_DSLASH_THREADS 128
 #endif
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
 
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
-                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv) {
+                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv, int rhs_block) {
     Args<R> a;
     a.U = links;
     a.in = in;
@@ -383,7 +384,9 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
     }
     a.V = g.V;
     a.g5 = e.g5;
-    const int by = nrhs > 1 ? 2 : 1, bx = DSLASH_THREADS / by;
+    int by = rhs_block > 0 ? rhs_block : (nrhs > 1 ? 2 : 1);
+    while (by > 1 && by > nrhs) by >>= 1;
+    const int bx = DSLASH_THREADS / by;
     dim3 block(bx, by);
     dim3 grid((g.V + bx - 1) / bx, (nrhs + by - 1) / by);
     if (deriv) dslash_kernel<R, true><<<grid, block, 0, s>>>(a, nrhs);
@@ -392,8 +395,8 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
 }
 
 template void launch_dslash<double>(const Geom&, double, const void*, const void*, void*, int, const double*,
-                                    const Epilogue&, cudaStream_t, bool);
+                                    const Epilogue&, cudaStream_t, bool, int);
 template void launch_dslash<float>(const Geom&, double, const void*, const void*, void*, int, const double*,
-                                   const Epilogue&, cudaStream_t, bool);
+                                   const Epilogue&, cudaStream_t, bool, int);
 
 }  // namespace ovl

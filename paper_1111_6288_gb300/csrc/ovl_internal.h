@@ -55,10 +55,12 @@ struct Epilogue {
 
 // ---- kernels: dslash.cu ---------------------------------------------------
 // deriv: apply dH_w/dphi (the phi-derivative of the x hops, per right-hand-side phase) in
-// place of H_w; the epilogue is the same.
+// place of H_w; the epilogue is the same.  rhs_block: right-hand sides per thread block
+// (1, 2 or 4; 0 = default).
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
-                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv = false);
+                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv = false,
+                   int rhs_block = 0);
 
 // ---- kernels: blas.cu -----------------------------------------------------
 // ABI spinor [rhs][site][12] (dtype_in: 0 complex128, 1 complex64) -> internal [rhs][12][V] of R.
