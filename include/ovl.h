@@ -126,7 +126,7 @@ int ov_create(const ov_params* p, ov_ctx** out);
 int ov_destroy(ov_ctx* ctx);
 /* Message of the last failure on ctx (or of the last ov_create failure if ctx is NULL). */
 const char* ov_last_error(const ov_ctx* ctx);
-/* Human-readable summary of the last eigensolver call on ctx (cycles, residuals, time). */
+/* Human-readable summary of the last eigensolver or solve call on ctx (cycles, residuals). */
 const char* ov_last_info(const ov_ctx* ctx);
 /* Timings of the Wilson-kernel right-hand-side blocks the library tried (1, 2 or 4 systems per
  * thread block) for each batch size it met; the fastest is used from then on. */

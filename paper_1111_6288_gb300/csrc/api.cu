@@ -929,6 +929,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     std::string hist;
     bool last_lo = true;
     int last_degree = 0;
+    double t_filter[2] = {0.0, 0.0}, t_ortho = 0.0, t_rr = 0.0;
     const auto t_start = std::chrono::steady_clock::now();
     for (int it = 0; it <= max_iter; ++it) {
         if (it > 0) {
@@ -941,10 +942,16 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
             const int degree = std::max(2, std::min(200, (int)std::ceil(std::acosh(amp) / std::acosh(z0))));
             last_lo = lo;
             last_degree = degree;
+            auto tf = std::chrono::steady_clock::now();
             if (lo) TRY(cheb_filter<float>(c, W, m, a, degree, d_phase, s));
             else TRY(cheb_filter<double>(c, W, m, a, degree, d_phase, s));
+            CK(cudaStreamSynchronize(s));
+            auto to = std::chrono::steady_clock::now();
+            t_filter[lo ? 0 : 1] += std::chrono::duration<double>(to - tf).count();
             TRY(cholqr2(c, W, m, W2, s));
+            t_ortho += std::chrono::duration<double>(std::chrono::steady_clock::now() - to).count();
         }
+        const auto t_rr0 = std::chrono::steady_clock::now();
         // Rayleigh-Ritz in two stages (FP64).  (1) With Q^2, the operator the filter acts on:
         // orders the block by Ritz values of Q^2 and gives the damping bound a.  Ordering by Q
         // instead would pick up mixtures of +lambda and -lambda eigenvectors (same Q^2, so the
@@ -997,6 +1004,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
         norm2_rhs<double>(tt, n12, n_ev, res.data(), c->d_partial, c->d_red, s);
         worst = 0.0;
         for (int i = 0; i < n_ev; ++i) worst = std::max(worst, std::sqrt(res[i]));
+        t_rr += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_rr0).count();
         char buf[96];
         snprintf(buf, sizeof(buf), "%s%s%d:%.1e", it ? " " : "", it == 0 ? "" : (last_lo ? "f32/" : "f64/"),
                  last_degree, worst);
@@ -1014,9 +1022,12 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
     CK(cudaStreamSynchronize(s));
     {
-        char buf[160];
-        snprintf(buf, sizeof(buf), "eigensolver: n_ev %d, block %d, %.1f s; per cycle [precision/degree:]worst residual: ",
-                 n_ev, m, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+        char buf[256];
+        snprintf(buf, sizeof(buf),
+                 "eigensolver: n_ev %d, block %d, %.1f s (filter f32 %.1f, f64 %.1f, orthonormalise %.1f, "
+                 "Rayleigh-Ritz %.1f); per cycle [precision/degree:]worst residual: ",
+                 n_ev, m, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(),
+                 t_filter[0], t_filter[1], t_ortho, t_rr);
         c->info = std::string(buf) + hist;
     }
     if (status != OV_OK)
@@ -1193,6 +1204,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
     }
     const double base_tol = c->p.inner_tol > 0.0 ? c->p.inner_tol : (prec == OV_PREC_F64 ? 0.0 : 1e-6);
     int outer = 0, inner_total = 0, status = OV_OK;
+    std::string hist = "solve:";
     const int max_outer = 60;
     while (true) {
         double worst = 0.0;
@@ -1267,10 +1279,18 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         CKL();
         ++outer;
         TRY(true_residual());
+        {
+            double worst = 0.0;
+            for (int j = 0; j < nrhs; ++j) worst = std::max(worst, res[j]);
+            char buf[96];
+            snprintf(buf, sizeof(buf), " | cycle %d: %d inner, %d systems, residual %.2e", outer, iters, ns, worst);
+            hist += buf;
+        }
     }
     launch_unpack_spinor<double>(X, x, OV_C128, V, nrhs, s);
     CKL();
     CK(cudaStreamSynchronize(s));
+    c->info = hist;
     if (st) {
         st->status = status;
         st->outer_iters = outer;

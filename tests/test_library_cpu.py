@@ -102,3 +102,61 @@ def test_library_polynomial_delta_matches_oracle(ovl, n, eps):
     want = chebyshev.approximation_error(chebyshev.chebyshev_coeffs(n, eps), eps)
     assert ctx.delta == pytest.approx(want, rel=0.05)
     ctx.close()
+
+
+def _raw_ctx(ovl, **kw):
+    p = ovl._ovl._Params()
+    p.dims[:] = list(kw.get("dims", (4, 4, 4, 4)))
+    p.bc[:] = [0, 0, 0, 1]
+    p.m0 = -1.5
+    p.eps = 0.01
+    p.poly_degree = 8
+    p.precision = 0
+    p.inner_precision = 0
+    p.max_nrhs = kw.get("max_nrhs", 2)
+    h = ctypes.c_void_p()
+    assert ovl.lib().ov_create(ctypes.byref(p), ctypes.byref(h)) == 0
+    return h
+
+
+def test_calls_before_a_gauge_field_are_rejected_on_the_host(ovl):
+    """No GPU work is started: the state check comes first (the pointers are never used)."""
+    L = ovl.lib()
+    h = _raw_ctx(ovl)
+    a, b = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000)
+    assert L.apply_wilson(h, a, b, 1, None, 1, None) == 9
+    assert b"gauge" in L.ov_last_error(h)
+    assert L.apply_sign_Hw(h, a, b, 1, None, None) == 9
+    assert L.apply_overlap(h, a, b, 1, 0.1, None, None) == 9
+    L.ov_destroy(h)
+
+
+def test_error_codes_for_invalid_arguments(ovl):
+    L = ovl.lib()
+    h = _raw_ctx(ovl)
+    a = ctypes.c_void_p(0x1000)
+    # eigensolver and deflate argument checks happen before any device work
+    lam = (ctypes.c_double * 4)()
+    assert L.ov_eigensolve_Q(h, 0.0, 4, 1e-8, 10, None, lam, 1, None) == 9  # no gauge yet
+    assert L.deflate(h, 0.0, a, None, 3, 0, None) == 1  # lambda missing
+    assert L.deflate(h, float("nan"), a, lam, 1, 0, None) == 1
+    assert L.deflate(h, 0.0, a, lam, 1, 7, None) == 1  # bad dtype
+    L.ov_destroy(h)
+    # a context that cannot be made reports through ov_last_error(NULL)
+    p = ovl._ovl._Params()
+    p.dims[:] = [4, 4, 4, 4]
+    p.eps = 0.5
+    p.poly_degree = 8
+    p.max_nrhs = 0
+    hh = ctypes.c_void_p()
+    assert L.ov_create(ctypes.byref(p), ctypes.byref(hh)) == 1
+    assert b"max_nrhs" in L.ov_last_error(None)
+
+
+def test_noalloc_rejects_oversize_without_a_gpu(ovl):
+    L = ovl.lib()
+    d = (ctypes.c_int * 4)(32, 32, 32, 32)
+    bc = (ctypes.c_int * 4)(0, 0, 0, 1)
+    rc = L.apply_wilson_noalloc(d, bc, -1.5, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(64), 1, None, 1,
+                                None)
+    assert rc == 1 and b"scratch" in L.ov_last_error(None)
