@@ -214,14 +214,13 @@ def run_reference(args):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_case():
-    """A few FP32 Wilson-kernel launches (plain and Clenshaw-epilogue) at 24^3 x 48."""
+def kernel_case(dims):
+    """A few FP32 Wilson-kernel launches (plain and Clenshaw-epilogue) on one lattice."""
     import torch
 
     import paper_1111_6288_gb300 as P
     import synth
 
-    dims = (24, 24, 24, 48)
     U = torch.from_numpy(synth.random_su3_field(dims, LINK_EPS, 0)).cuda()
     ctx = P.Context(P.Params(dims=dims, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=4, precision=P.OV_PREC_F32,
                              inner_precision=P.OV_PREC_F32, max_nrhs=1))
@@ -244,8 +243,9 @@ def main():
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the FP64-only comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
-                    help="profiling case: a few FP32 Wilson-kernel launches on 24^3x48 (links 191 MB > L2), "
+                    help="profiling case: a few FP32 Wilson-kernel launches (default 24^3x48), "
                          "then exit without a JSON line")
+    ap.add_argument("--kernel-dims", default="24,24,24,48", help="lattice of the profiling case: Lx,Ly,Lz,Lt")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -254,7 +254,7 @@ def main():
         run_reference(args)
         return
     if args.kernel_case:
-        kernel_case()
+        kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")))
         return
 
     import numpy as np

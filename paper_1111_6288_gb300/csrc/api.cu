@@ -519,10 +519,11 @@ int apply_generic(ov_ctx* c, const void* in, void* out, int nrhs, const double* 
 // ---- block helpers for orthonormalisation and Rayleigh-Ritz (FP64) ----------------
 
 // Gram matrix G = W^+ W (m x m) to host, column-major.
+template <typename R = double>
 int gram_host(ov_ctx* c, const void* A, int na, const void* B, int nb, std::vector<HostCplx>& H, cudaStream_t s) {
     const long long n12 = 12LL * c->g.V;
     TRY(ensure_small(c, (long long)na * nb, (long long)na * nb * 4 * 152, 1));
-    multidot<double>(A, n12, na, B, n12, nb, n12, c->d_C, c->d_partial, c->partial_cap, s);
+    multidot<R>(A, n12, na, B, n12, nb, n12, c->d_C, c->d_partial, c->partial_cap, s);
     CKL();
     std::vector<double2> tmp((size_t)na * nb);
     CK(cudaMemcpyAsync(tmp.data(), c->d_C, sizeof(double2) * na * nb, cudaMemcpyDeviceToHost, s));
@@ -534,6 +535,7 @@ int gram_host(ov_ctx* c, const void* A, int na, const void* B, int nb, std::vect
 }
 
 // out_j = sum_i A_i M(i, j), M column-major na x nb on the host.
+template <typename R = double>
 int rotate(ov_ctx* c, const void* A, int na, const std::vector<HostCplx>& M, int nb, void* out, cudaStream_t s) {
     const long long n12 = 12LL * c->g.V;
     TRY(ensure_small(c, (long long)na * nb, 0, 1));
@@ -541,7 +543,7 @@ int rotate(ov_ctx* c, const void* A, int na, const std::vector<HostCplx>& M, int
     for (int i = 0; i < na; ++i)
         for (int j = 0; j < nb; ++j) tmp[(size_t)i * nb + j] = make_double2(M[i + (size_t)j * na].re, M[i + (size_t)j * na].im);
     CK(cudaMemcpyAsync(c->d_C, tmp.data(), sizeof(double2) * na * nb, cudaMemcpyHostToDevice, s));
-    combine<double>(A, n12, na, c->d_C, nb, nb, 0.0, nullptr, n12, out, n12, n12, s);
+    combine<R>(A, n12, na, c->d_C, nb, nb, 0.0, nullptr, n12, out, n12, n12, s);
     CKL();
     CK(cudaStreamSynchronize(s));
     return OV_OK;
@@ -560,16 +562,18 @@ void hermitize(std::vector<HostCplx>& T, int n) {
     }
 }
 
-// Cholesky-QR, twice: W (m vectors, FP64) <- W R with W^+ W = 1.  tmp: m vectors.
+// Cholesky-QR, twice: W (m vectors of precision R) <- W R with W^+ W = 1 (Gram and
+// triangular factors in FP64 on the host).  tmp: m vectors.
+template <typename R = double>
 int cholqr2(ov_ctx* c, void* W, int m, void* tmp, cudaStream_t s) {
     for (int pass = 0; pass < 2; ++pass) {
         std::vector<HostCplx> G, Rm;
-        TRY(gram_host(c, W, m, W, m, G, s));
+        TRY(gram_host<R>(c, W, m, W, m, G, s));
         hermitize(G, m);
         if (!host_cholesky(m, G)) return fail(c, OV_ERR_BREAKDOWN, "Cholesky-QR: Gram matrix not positive definite");
         host_inv_lower_dag(m, G, Rm);
-        TRY(rotate(c, W, m, Rm, m, tmp, s));
-        CK(cudaMemcpyAsync(W, tmp, vec_bytes(c, OV_PREC_F64) * m, cudaMemcpyDeviceToDevice, s));
+        TRY(rotate<R>(c, W, m, Rm, m, tmp, s));
+        CK(cudaMemcpyAsync(W, tmp, vec_bytes(c, prec_of<R>()) * m, cudaMemcpyDeviceToDevice, s));
     }
     return OV_OK;
 }
@@ -617,21 +621,13 @@ int register_bank_internal(ov_ctx* c, double phase, const void* W64, int n, cons
 }
 
 // Chebyshev filter W <- T_d(Z) W (then normalised by the caller), Z = (2 Q^2 - (1 + a))/(1 - a),
-// which damps the part of the spectrum of Q^2 in [a, 1] and amplifies [0, a).  W is FP64;
-// the recurrence runs in precision R.
+// which damps the part of the spectrum of Q^2 in [a, 1] and amplifies [0, a).  W: m vectors of
+// precision R.
 template <typename R>
-int cheb_filter(ov_ctx* c, void* W64, int m, double a, int degree, const double* d_phase, cudaStream_t s) {
+int cheb_filter(ov_ctx* c, void* W, int m, double a, int degree, const double* d_phase, cudaStream_t s) {
     const int prec = prec_of<R>();
-    const long long n = 12LL * c->g.V * m;
     const size_t vb = vec_bytes(c, prec);
-    void *W, *Tm, *Tc, *tt;
-    if (std::is_same<R, double>::value) {
-        W = W64;
-    } else {
-        TRY(workspace(c, "flt_W", prec, m, &W));
-        launch_convert<double, float>(W64, W, c->g.V, m, s);
-        CKL();
-    }
+    void *Tm, *Tc, *tt;
     TRY(workspace(c, "flt_Tm", prec, m, &Tm));
     TRY(workspace(c, "flt_Tc", prec, m, &Tc));
     TRY(workspace(c, "flt_t", prec, m, &tt));
@@ -661,12 +657,68 @@ int cheb_filter(ov_ctx* c, void* W64, int m, double a, int degree, const double*
     }
     CKL();
     c->dslash_count += 2LL * degree * m;
-    if (std::is_same<R, double>::value) {
-        CK(cudaMemcpyAsync(W64, tk, vb * m, cudaMemcpyDeviceToDevice, s));
-    } else {
-        launch_convert<float, double>(tk, W64, c->g.V, m, s);
-        CKL();
+    CK(cudaMemcpyAsync(W, tk, vb * m, cudaMemcpyDeviceToDevice, s));
+    return OV_OK;
+}
+
+// Two-stage Rayleigh-Ritz on the block W (m vectors of precision R; Gram matrices and their
+// eigenproblems in FP64 on the host).  (1) With Q^2, the operator the filter acts on: orders the
+// block by Ritz values of Q^2 and gives the damping bound a.  Ordering by Q instead would pick up
+// mixtures of +lambda and -lambda eigenvectors (same Q^2, so the filter never separates them)
+// whose Q Rayleigh quotient is near zero.  (2) With Q inside the first n_ev columns: resolves the
+// signs; ordered by |theta|.  On return W (and QW) hold the rotated block, theta the Ritz values
+// of the first n_ev columns and res their squared residuals ||Q w - theta w||^2.
+template <typename R>
+int eig_rayleigh_ritz(ov_ctx* c, int m, int n_ev, void*& W, void*& W2, void*& QW, void*& QW2, void* tt,
+                      const double* d_phase, std::vector<double>& theta, std::vector<double>& res, double& a,
+                      cudaStream_t s) {
+    const long long n12 = 12LL * c->g.V;
+    const size_t vb = vec_bytes(c, prec_of<R>());
+    const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
+    Epilogue eq;
+    eq.c_op = 1.0 / c->hw_norm;
+    launch_dslash<R>(c->g, c->p.m0, U, W, QW, m, d_phase, eq, s);
+    CKL();
+    c->dslash_count += m;
+    {
+        std::vector<HostCplx> G2, Y;
+        std::vector<double> mu;
+        TRY(gram_host<R>(c, QW, m, QW, m, G2, s));
+        hermitize(G2, m);
+        host_eigh(m, G2, mu, Y);
+        a = std::min(mu[m - 1], 0.95);
+        TRY(rotate<R>(c, W, m, Y, m, W2, s));
+        TRY(rotate<R>(c, QW, m, Y, m, QW2, s));
+        std::swap(W, W2);
+        std::swap(QW, QW2);
     }
+    std::vector<HostCplx> T, Z;
+    TRY(gram_host<R>(c, W, n_ev, QW, n_ev, T, s));
+    hermitize(T, n_ev);
+    std::vector<double> w;
+    host_eigh(n_ev, T, w, Z);
+    std::vector<int> order(n_ev);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+        return std::fabs(w[i]) < std::fabs(w[j]) || (std::fabs(w[i]) == std::fabs(w[j]) && w[i] < w[j]);
+    });
+    std::vector<HostCplx> Zs((size_t)n_ev * n_ev);
+    for (int j = 0; j < n_ev; ++j) {
+        theta[j] = w[order[j]];
+        for (int i = 0; i < n_ev; ++i) Zs[i + (size_t)j * n_ev] = Z[i + (size_t)order[j] * n_ev];
+    }
+    // rotate the first n_ev columns in place (through W2/QW2): the block's span is unchanged
+    TRY(rotate<R>(c, W, n_ev, Zs, n_ev, W2, s));
+    TRY(rotate<R>(c, QW, n_ev, Zs, n_ev, QW2, s));
+    CK(cudaMemcpyAsync(W, W2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(QW, QW2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> mth(n_ev), ones(n_ev, 1.0);
+    for (int i = 0; i < n_ev; ++i) mth[i] = -theta[i];
+    CK(cudaMemcpyAsync(tt, QW, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    launch_axpby<R>(mth.data(), W, ones.data(), tt, n12, n_ev, s);
+    CKL();
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * m, m));
+    norm2_rhs<R>(tt, n12, n_ev, res.data(), c->d_partial, c->d_red, s);
     return OV_OK;
 }
 
@@ -898,27 +950,33 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     // wanted set ends in (near-degenerate modes at the cut converge at the rate set by a)
     const int m = std::min(std::min(n_ev + std::max(16, n_ev), 12 * c->g.V), kMaxRhs);
     const long long n12 = 12LL * c->g.V;
-    const size_t vb = vec_bytes(c, OV_PREC_F64);
-    void *W, *W2, *QW, *QW2, *tt;
+    // the block lives in FP32 while the residuals are well above FP32 resolution (filter,
+    // Cholesky-QR and Rayleigh-Ritz all on FP32 vectors), then in FP64
+    void *W, *W2, *QW, *QW2, *tt, *Wf, *W2f, *QWf, *QW2f, *ttf;
     TRY(workspace(c, "eig_W", OV_PREC_F64, m, &W));
     TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
     TRY(workspace(c, "eig_QW", OV_PREC_F64, m, &QW));
     TRY(workspace(c, "eig_QW2", OV_PREC_F64, m, &QW2));
     TRY(workspace(c, "eig_t", OV_PREC_F64, m, &tt));
+    TRY(workspace(c, "eig_W", OV_PREC_F32, m, &Wf));
+    TRY(workspace(c, "eig_W2", OV_PREC_F32, m, &W2f));
+    TRY(workspace(c, "eig_QW", OV_PREC_F32, m, &QWf));
+    TRY(workspace(c, "eig_QW2", OV_PREC_F32, m, &QW2f));
+    TRY(workspace(c, "eig_t", OV_PREC_F32, m, &ttf));
     random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)W, n12 * m, 0x5eed0f0e1ULL);
     count_launch();
     CKL();
-    TRY(cholqr2(c, W, m, W2, s));
+    launch_convert<double, float>(W, Wf, c->g.V, m, s);
+    CKL();
+    TRY(cholqr2<float>(c, Wf, m, W2f, s));
     SysSet S;
     S.n = m;
     S.phase.assign(m, phase);
     TRY(upload_sys(c, S, s));
     const double* d_phase = phase != 0.0 ? c->d_phase : nullptr;
-    const double h = c->hw_norm;
-    // The filter runs in FP32 while the residuals are well above FP32 resolution, then in FP64.
-    // Its degree is chosen each cycle so that the largest amplification, |T_d(z(0))| with
-    // z(0) = -(1 + a)/(1 - a), stays below amp: a larger spread between the filtered columns
-    // would collapse the block below the resolution of the Cholesky-QR step.
+    // The filter degree is chosen each cycle so that the largest amplification, |T_d(z(0))|
+    // with z(0) = -(1 + a)/(1 - a), stays below amp: a larger spread between the filtered
+    // columns would collapse the block below the resolution of the Cholesky-QR step.
     const double switch_res = 3e-6;
     double prev_worst = 1e300;
     bool in_f64 = false;
@@ -927,92 +985,56 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     double worst = 1e300;
     int status = OV_ERR_NOT_CONVERGED;
     std::string hist;
-    bool last_lo = true;
-    int last_degree = 0;
     double t_filter[2] = {0.0, 0.0}, t_ortho = 0.0, t_rr = 0.0;
     const auto t_start = std::chrono::steady_clock::now();
+    auto since = [](std::chrono::steady_clock::time_point t0) {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
     for (int it = 0; it <= max_iter; ++it) {
+        int degree = 0;
         if (it > 0) {
-            // FP32 until the residual reaches switch_res or stops improving, then FP64
-            if (!in_f64 && (worst <= switch_res || (worst < 1e-4 && worst > 0.9 * prev_worst))) in_f64 = true;
+            if (!in_f64 && (worst <= switch_res || (worst < 1e-4 && worst > 0.9 * prev_worst))) {
+                // FP32 -> FP64: widen the block and restore FP64 orthonormality
+                launch_convert<float, double>(Wf, W, c->g.V, m, s);
+                CKL();
+                auto t0 = std::chrono::steady_clock::now();
+                TRY(cholqr2<double>(c, W, m, W2, s));
+                t_ortho += since(t0);
+                in_f64 = true;
+            }
             prev_worst = worst;
-            const bool lo = !in_f64;
-            const double amp = lo ? 1e3 : 1e6;
+            const double amp = in_f64 ? 1e6 : 1e3;
             const double z0 = (1.0 + a) / (1.0 - a);
-            const int degree = std::max(2, std::min(200, (int)std::ceil(std::acosh(amp) / std::acosh(z0))));
-            last_lo = lo;
-            last_degree = degree;
+            degree = std::max(2, std::min(200, (int)std::ceil(std::acosh(amp) / std::acosh(z0))));
             auto tf = std::chrono::steady_clock::now();
-            if (lo) TRY(cheb_filter<float>(c, W, m, a, degree, d_phase, s));
-            else TRY(cheb_filter<double>(c, W, m, a, degree, d_phase, s));
+            if (in_f64) TRY(cheb_filter<double>(c, W, m, a, degree, d_phase, s));
+            else TRY(cheb_filter<float>(c, Wf, m, a, degree, d_phase, s));
             CK(cudaStreamSynchronize(s));
             auto to = std::chrono::steady_clock::now();
-            t_filter[lo ? 0 : 1] += std::chrono::duration<double>(to - tf).count();
-            TRY(cholqr2(c, W, m, W2, s));
-            t_ortho += std::chrono::duration<double>(std::chrono::steady_clock::now() - to).count();
+            t_filter[in_f64 ? 1 : 0] += std::chrono::duration<double>(to - tf).count();
+            if (in_f64) TRY(cholqr2<double>(c, W, m, W2, s));
+            else TRY(cholqr2<float>(c, Wf, m, W2f, s));
+            t_ortho += since(to);
         }
         const auto t_rr0 = std::chrono::steady_clock::now();
-        // Rayleigh-Ritz in two stages (FP64).  (1) With Q^2, the operator the filter acts on:
-        // orders the block by Ritz values of Q^2 and gives the damping bound a.  Ordering by Q
-        // instead would pick up mixtures of +lambda and -lambda eigenvectors (same Q^2, so the
-        // filter never separates them) whose Q Rayleigh quotient is near zero.  (2) With Q
-        // inside the first n_ev columns: resolves the signs; ordered by |theta|.
-        Epilogue eq;
-        eq.c_op = 1.0 / h;
-        launch_dslash<double>(c->g, c->p.m0, c->U64, W, QW, m, d_phase, eq, s);
-        CKL();
-        c->dslash_count += m;
-        {
-            std::vector<HostCplx> G2, Y;
-            std::vector<double> mu;
-            TRY(gram_host(c, QW, m, QW, m, G2, s));
-            hermitize(G2, m);
-            host_eigh(m, G2, mu, Y);
-            a = std::min(mu[m - 1], 0.95);
-            TRY(rotate(c, W, m, Y, m, W2, s));
-            TRY(rotate(c, QW, m, Y, m, QW2, s));
-            std::swap(W, W2);
-            std::swap(QW, QW2);
-        }
-        std::vector<HostCplx> T, Z;
-        TRY(gram_host(c, W, n_ev, QW, n_ev, T, s));
-        hermitize(T, n_ev);
-        std::vector<double> w;
-        host_eigh(n_ev, T, w, Z);
-        std::vector<int> order(n_ev);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
-            return std::fabs(w[i]) < std::fabs(w[j]) || (std::fabs(w[i]) == std::fabs(w[j]) && w[i] < w[j]);
-        });
-        std::vector<HostCplx> Zs((size_t)n_ev * n_ev);
-        for (int j = 0; j < n_ev; ++j) {
-            theta[j] = w[order[j]];
-            for (int i = 0; i < n_ev; ++i) Zs[i + (size_t)j * n_ev] = Z[i + (size_t)order[j] * n_ev];
-        }
-        // rotate the first n_ev columns in place (through W2/QW2): the block's span is unchanged
-        TRY(rotate(c, W, n_ev, Zs, n_ev, W2, s));
-        TRY(rotate(c, QW, n_ev, Zs, n_ev, QW2, s));
-        CK(cudaMemcpyAsync(W, W2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(QW, QW2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
-        // residuals r_i = Q w_i - theta_i w_i, i < n_ev
-        std::vector<double> mth(n_ev), ones(n_ev, 1.0);
-        for (int i = 0; i < n_ev; ++i) mth[i] = -theta[i];
-        CK(cudaMemcpyAsync(tt, QW, vb * n_ev, cudaMemcpyDeviceToDevice, s));
-        launch_axpby<double>(mth.data(), W, ones.data(), tt, n12, n_ev, s);
-        CKL();
-        TRY(ensure_small(c, 0, (long long)kRedBlocks * m, m));
-        norm2_rhs<double>(tt, n12, n_ev, res.data(), c->d_partial, c->d_red, s);
+        if (in_f64) TRY(eig_rayleigh_ritz<double>(c, m, n_ev, W, W2, QW, QW2, tt, d_phase, theta, res, a, s));
+        else TRY(eig_rayleigh_ritz<float>(c, m, n_ev, Wf, W2f, QWf, QW2f, ttf, d_phase, theta, res, a, s));
+        t_rr += since(t_rr0);
         worst = 0.0;
         for (int i = 0; i < n_ev; ++i) worst = std::max(worst, std::sqrt(res[i]));
-        t_rr += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_rr0).count();
         char buf[96];
-        snprintf(buf, sizeof(buf), "%s%s%d:%.1e", it ? " " : "", it == 0 ? "" : (last_lo ? "f32/" : "f64/"),
-                 last_degree, worst);
+        snprintf(buf, sizeof(buf), "%s%s%d:%.1e", it ? " " : "", it == 0 ? "" : (in_f64 ? "f64/" : "f32/"), degree,
+                 worst);
         hist += buf;
         if (worst <= tol) {
             status = OV_OK;
             break;
         }
+    }
+    if (!in_f64) {  // converged (or stopped) in FP32: hand out FP64 vectors
+        launch_convert<float, double>(Wf, W, c->g.V, m, s);
+        CKL();
+        TRY(cholqr2<double>(c, W, m, W2, s));
     }
     for (int i = 0; i < n_ev; ++i) lambda_out[i] = theta[i];
     if (V_out) {
@@ -1026,8 +1048,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
         snprintf(buf, sizeof(buf),
                  "eigensolver: n_ev %d, block %d, %.1f s (filter f32 %.1f, f64 %.1f, orthonormalise %.1f, "
                  "Rayleigh-Ritz %.1f); per cycle [precision/degree:]worst residual: ",
-                 n_ev, m, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(),
-                 t_filter[0], t_filter[1], t_ortho, t_rr);
+                 n_ev, m, since(t_start), t_filter[0], t_filter[1], t_ortho, t_rr);
         c->info = std::string(buf) + hist;
     }
     if (status != OV_OK)

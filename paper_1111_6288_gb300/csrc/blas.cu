@@ -357,19 +357,24 @@ __global__ void multidot_sum_k(const double2* __restrict__ partial, int nchunk, 
     C[idx] = v;
 }
 
-// out_j = alpha X_j + sum_i A_i C[i][j], up to CJ outputs per launch
+// out_j = alpha X_j + sum_i A_i C[i][j], up to CJ outputs per launch; the coefficients are
+// converted once to the data precision R in shared memory.
 constexpr int CJ = 8;
 template <typename R>
 __global__ void __launch_bounds__(256) combine_k(const typename C2<R>::T* __restrict__ A, long long sA, int na,
                                                  const double2* __restrict__ C, int ldc, int j0, int nj, double alpha,
                                                  const typename C2<R>::T* __restrict__ X, long long sX,
                                                  typename C2<R>::T* __restrict__ out, long long sO, long long n) {
-    extern __shared__ double2 shC[];  // [na][CJ]
+    extern __shared__ unsigned char cmb_raw[];
+    typename C2<R>::T* shC = (typename C2<R>::T*)cmb_raw;  // [na][CJ]
     for (int q = threadIdx.x; q < na * CJ; q += blockDim.x) {
         const int i = q / CJ, j = q % CJ;
-        shC[q] = (j < nj) ? C[(long long)i * ldc + j0 + j] : make_double2(0, 0);
+        const double2 c = (j < nj) ? C[(long long)i * ldc + j0 + j] : make_double2(0, 0);
+        shC[q].x = (R)c.x;
+        shC[q].y = (R)c.y;
     }
     __syncthreads();
+    const R al = (R)alpha;
     for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
         R accr[CJ], acci[CJ];
 #pragma unroll
@@ -378,9 +383,9 @@ __global__ void __launch_bounds__(256) combine_k(const typename C2<R>::T* __rest
             typename C2<R>::T a = A[(long long)i * sA + m];
 #pragma unroll
             for (int j = 0; j < CJ; ++j) {
-                const double2 c = shC[i * CJ + j];
-                accr[j] += a.x * (R)c.x - a.y * (R)c.y;
-                acci[j] += a.x * (R)c.y + a.y * (R)c.x;
+                const typename C2<R>::T c = shC[i * CJ + j];
+                accr[j] += a.x * c.x - a.y * c.y;
+                acci[j] += a.x * c.y + a.y * c.x;
             }
         }
         for (int j = 0; j < nj; ++j) {
@@ -389,8 +394,8 @@ __global__ void __launch_bounds__(256) combine_k(const typename C2<R>::T* __rest
             o.y = acci[j];
             if (X) {
                 typename C2<R>::T xv = X[(long long)(j0 + j) * sX + m];
-                o.x += (R)alpha * xv.x;
-                o.y += (R)alpha * xv.y;
+                o.x += al * xv.x;
+                o.y += al * xv.y;
             }
             out[(long long)(j0 + j) * sO + m] = o;
         }
@@ -632,7 +637,9 @@ void multidot(const void* A, long long strideA, int na, const void* B, long long
               double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s) {
     const int ti = (na + MT - 1) / MT, tj = (nb + MT - 1) / MT;
     // enough chunks to fill the GPU about four times over, bounded by the partial buffer
-    long long nchunk = (4LL * 152 + ti * tj - 1) / (ti * tj);
+    // enough chunks to fill the GPU, and chunks of at most 4096 elements (each thread's partial
+    // sum then covers about 1000 products, short enough for FP32 accumulation)
+    long long nchunk = std::max((4LL * 152 + ti * tj - 1) / (ti * tj), (n + 4095) / 4096);
     const long long max_chunk_by_cap = partial_cap / ((long long)na * nb);
     if (nchunk > max_chunk_by_cap) nchunk = max_chunk_by_cap;
     if (nchunk < 1) nchunk = 1;
@@ -651,7 +658,7 @@ void multidot(const void* A, long long strideA, int na, const void* B, long long
 template <typename R>
 void combine(const void* A, long long strideA, int na, const double2* d_C, int ldc, int nb, double alpha,
              const void* X, long long strideX, void* out, long long strideO, long long n, cudaStream_t s) {
-    const size_t shm = sizeof(double2) * (size_t)na * CJ;
+    const size_t shm = sizeof(typename C2<R>::T) * (size_t)na * CJ;
     for (int j0 = 0; j0 < nb; j0 += CJ) {
         const int nj = (nb - j0 < CJ) ? nb - j0 : CJ;
         combine_k<R><<<grid_for(n, 256, 152 * 8), 256, shm, s>>>(
