@@ -49,8 +49,9 @@ METRIC = "D_ov applies/s, dslash HBM GB/s, time-to-1e-10 solve (mixed vs FP64)"
 UNIT = "D_ov applies/s"
 WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV}, m={MASS}, tol={TOL}"
 # ncu: DRAM bytes of the FP32 Wilson kernel over its algorithmic bytes (plain and Clenshaw-epilogue
-# launches, 24^3x48 capture); update together with profiles/ whenever the kernel changes
-DRAM_OVER_ALGORITHMIC = 0.965
+# launches, 24^3x48 capture); None until the current kernel has been captured.  Update together
+# with profiles/ whenever the kernel changes.
+DRAM_OVER_ALGORITHMIC = None
 
 
 def dist_env():
@@ -391,7 +392,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 # DRAM bytes per launch: ncu dram__bytes_read + write of this kernel measured 0.965 of its
                 # algorithmic bytes (profiles/dslash_f32_24x24x24x48_ncu_full.md), scaled to this launch mix
-                "traffic": DRAM_OVER_ALGORITHMIC * bytes_per_launch, "traffic_unit": "B/launch",
+                "traffic": DRAM_OVER_ALGORITHMIC * bytes_per_launch if DRAM_OVER_ALGORITHMIC else None,
+                "traffic_unit": "B/launch",
                 "peak_source": peak_kind,
                 "kernel": "dslash_kernel<float> (Clenshaw step launches, 16^3x32, 1-2 systems per launch)",
                 "avg_launch_us": 1e3 * prof32["clenshaw_ms"] / max(prof32["clenshaw_launches"], 1),

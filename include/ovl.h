@@ -128,8 +128,9 @@ int ov_destroy(ov_ctx* ctx);
 const char* ov_last_error(const ov_ctx* ctx);
 /* Human-readable summary of the last eigensolver or solve call on ctx (cycles, residuals). */
 const char* ov_last_info(const ov_ctx* ctx);
-/* Timings of the Wilson-kernel right-hand-side blocks the library tried (1, 2 or 4 systems per
- * thread block) for each batch size it met; the fastest is used from then on. */
+/* Timings of the Wilson-kernel launch shapes the library tried for each batch size it met
+ * (1, 2 or 4 systems per thread block; "d": FP32 registers capped for 7 resident blocks per SM
+ * instead of 6); the fastest is used from then on. */
 const char* ov_tune_info(const ov_ctx* ctx);
 /* Number of lattice sites. */
 long long ov_volume(const ov_ctx* ctx);

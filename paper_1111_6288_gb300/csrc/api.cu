@@ -18,6 +18,7 @@
 #include <map>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ovl.h"
@@ -79,7 +80,7 @@ struct ov_ctx {
     // CUDA graphs of the Clenshaw loop, keyed by precision, systems and buffers
     bool use_graphs = true;
     // autotuned right-hand sides per Wilson-kernel block, keyed by precision and systems
-    std::map<std::pair<int, int>, int> rhs_block;
+    std::map<std::pair<int, int>, int> launch_shape;
     std::string tune_log;
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, std::pair<cudaGraphExec_t, void*>> graphs;  // exec, buffer holding p
@@ -252,16 +253,23 @@ bool any_phase(const SysSet& S) {
     return false;
 }
 
-// Right-hand sides per Wilson-kernel block for ns systems of precision R: timed once on the
-// sign pipeline's own buffers (the Clenshaw-step launch with its epilogue), fastest kept.
+// Launch shape of the Wilson kernel for ns systems of precision R (right-hand sides per block,
+// and in FP32 the 6- or 7-blocks-per-SM register budget): timed once on the sign pipeline's own
+// buffers (the Clenshaw-step launch with its epilogue), fastest kept.
 template <typename R>
-int tuned_rhs_block(ov_ctx* c, int ns, const void* U, const double* d_phase, void* in, void* v1, void* v2,
-                    void* v3, void* out, cudaStream_t s) {
+int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* in, void* v1, void* v2,
+                void* v3, void* out, cudaStream_t s) {
     const auto key = std::make_pair(prec_of<R>(), ns);
-    auto it = c->rhs_block.find(key);
-    if (it != c->rhs_block.end()) return it->second;
-    int best = 1;
-    if (ns > 1) {
+    auto it = c->launch_shape.find(key);
+    if (it != c->launch_shape.end()) return it->second;
+    std::vector<int> shapes;
+    for (int by : {1, 2, 4}) {
+        if (by > ns) break;
+        shapes.push_back(by);
+        if (std::is_same<R, float>::value) shapes.push_back(by | kShapeDense);
+    }
+    int best = shapes[0];
+    if (shapes.size() > 1) {
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -275,28 +283,27 @@ int tuned_rhs_block(ov_ctx* c, int ns, const void* U, const double* d_phase, voi
         e.c3 = 1e-3;
         e.v3 = v3;
         char buf[64];
-        for (int by : {1, 2, 4}) {
-            if (by > ns) break;
-            launch_dslash<R>(c->g, c->p.m0, U, in, out, ns, d_phase, e, s, false, by);  // warm
+        for (int sh : shapes) {
+            launch_dslash<R>(c->g, c->p.m0, U, in, out, ns, d_phase, e, s, false, sh);  // warm
             cudaEventRecord(e0, s);
-            for (int q = 0; q < 5; ++q) launch_dslash<R>(c->g, c->p.m0, U, in, out, ns, d_phase, e, s, false, by);
+            for (int q = 0; q < 5; ++q) launch_dslash<R>(c->g, c->p.m0, U, in, out, ns, d_phase, e, s, false, sh);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            snprintf(buf, sizeof(buf), "%s%d:%.1fus", by == 1 ? "" : " ", by, 1e3f * ms / 5);
+            snprintf(buf, sizeof(buf), "%s%d%s:%.1fus", sh == shapes[0] ? "" : " ", sh & kShapeRhsMask,
+                     (sh & kShapeDense) ? "d" : "", 1e3f * ms / 5);
             c->tune_log += buf;
             if (ms < best_ms) {
                 best_ms = ms;
-                best = by;
+                best = sh;
             }
         }
         c->tune_log += "; ";
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        c->dslash_count += 0;  // tuning launches are not part of any operator application
     }
-    c->rhs_block[key] = best;
+    c->launch_shape[key] = best;
     return best;
 }
 
@@ -370,7 +377,7 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     const double link_cplx = std::is_same<R, double>::value ? 36.0 : 24.0;
     // the whole recurrence (2n launches, no host work) as one stream sequence
     // timing launches read t, bA, x_perp and write bB only (rewritten by the recurrence below)
-    const int rb = tuned_rhs_block<R>(c, ns, U, d_phase, t, bA, xperp, bA, bB, s);
+    const int rb = tuned_shape<R>(c, ns, U, d_phase, t, bA, xperp, bA, bB, s);
     auto enqueue = [&](cudaStream_t st) -> void* {
         launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, st);
         void* b1 = bA;
@@ -886,8 +893,8 @@ int ov_set_gauge(ov_ctx* c, const void* U, int dtype, ov_stream_t stream) {
             return fail(c, OV_ERR_OOM, "gauge field allocation failed");
         }
     }
-    launch_pack_gauge<double>(U, dtype, c->U64, c->g.V, s);
-    launch_pack_gauge<float>(U, dtype, c->U32, c->g.V, s);
+    launch_pack_gauge<double>(U, dtype, c->U64, c->g, s);
+    launch_pack_gauge<float>(U, dtype, c->U32, c->g, s);
     CKL();
     c->gauge_set = true;
     return OV_OK;
@@ -1367,7 +1374,6 @@ namespace {
 // the sign function; coef: device [ns][n+1]).
 int poly_per_system(ov_ctx* c, const void* X, const SysSet& S, const double* d_coef, void* Yout, cudaStream_t s) {
     const int ns = S.n;
-    const long long n12 = 12LL * c->g.V;
     void *bA, *bB, *t;
     TRY(workspace(c, "pp_bA", OV_PREC_F64, ns, &bA));
     TRY(workspace(c, "pp_bB", OV_PREC_F64, ns, &bB));
@@ -1590,7 +1596,6 @@ int tangent_poly(ov_ctx* c, const void* X, const SysSet& S, void* Y, cudaStream_
 
 // out = d sign(H_w)/dphi X (FP64 internal vectors), per run of equal phase.
 int dsign_dphi(ov_ctx* c, const void* X, const SysSet& Sall, void* out, cudaStream_t s) {
-    const long long n12 = 12LL * c->g.V;
     const size_t vb = vec_bytes(c, OV_PREC_F64);
     void *Xp, *Yt, *T1;
     TRY(workspace(c, "ds_Xp", OV_PREC_F64, Sall.n, &Xp));

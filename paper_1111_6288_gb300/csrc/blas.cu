@@ -122,18 +122,26 @@ __global__ void unpack_spinor_k(const void* __restrict__ in, TO* __restrict__ ab
     }
 }
 
-// FP64 links: 9 planes of double2 per direction.  FP32 links: rows 0 and 1 of U in
-// 3 planes of float4 per direction (entries (0,0)(0,1) | (0,2)(1,0) | (1,1)(1,2)); the
-// Wilson kernel rebuilds row 2 = conj(row0 x row1), exact for SU(3) links.
+// FP64 links: 9 planes of double2 per direction, the link U_mu(n) on the last slice of
+// direction mu multiplied by that direction's boundary factor when it is -1 (antiperiodic), so
+// that the FP64 Wilson kernel needs no boundary multiply (Dirichlet hops are skipped there).
+// FP32 links: rows 0 and 1 of U in 3 planes of float4 per direction (entries (0,0)(0,1) |
+// (0,2)(1,0) | (1,1)(1,2)); the Wilson kernel rebuilds row 2 = conj(row0 x row1), exact for
+// SU(3) links (and so for no link with a sign folded in: FP32 hops apply the factor).
 template <typename TI>
-__global__ void pack_gauge64_k(const TI* __restrict__ abi, double2* __restrict__ out, int V) {
+__global__ void pack_gauge64_k(const TI* __restrict__ abi, double2* __restrict__ out, Geom g) {
+    const int V = g.V;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 4LL * V) return;
     const int mu = (int)(idx / V), s = (int)(idx % V);
+    int stride = 1;
+    for (int nu = 0; nu < mu; ++nu) stride *= g.L[nu];
+    const int xmu = (s / stride) % g.L[mu];
+    const double f = (xmu == g.L[mu] - 1 && g.bcf[mu] == -1.0) ? -1.0 : 1.0;
     const TI* src = abi + ((long long)mu * V + s) * 9;
     double2* dst = out + (long long)mu * 9 * V + s;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) dst[(long long)k * V] = make_double2((double)src[k].x, (double)src[k].y);
+    for (int k = 0; k < 9; ++k) dst[(long long)k * V] = make_double2(f * (double)src[k].x, f * (double)src[k].y);
 }
 
 template <typename TI>
@@ -543,12 +551,13 @@ void launch_unpack_spinor(const void* internal, void* abi, int dtype_out, int V,
 }
 
 template <typename R>
-void launch_pack_gauge(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s) {
+void launch_pack_gauge(const void* abi, int dtype_in, void* internal, const Geom& geom, cudaStream_t s) {
+    const int V = geom.V;
     const long long n = 4LL * V;
     const int g = (int)((n + 255) / 256);
     if (std::is_same<R, double>::value) {
-        if (dtype_in == 0) pack_gauge64_k<double2><<<g, 256, 0, s>>>((const double2*)abi, (double2*)internal, V);
-        else pack_gauge64_k<float2><<<g, 256, 0, s>>>((const float2*)abi, (double2*)internal, V);
+        if (dtype_in == 0) pack_gauge64_k<double2><<<g, 256, 0, s>>>((const double2*)abi, (double2*)internal, geom);
+        else pack_gauge64_k<float2><<<g, 256, 0, s>>>((const float2*)abi, (double2*)internal, geom);
     } else {
         if (dtype_in == 0) pack_gauge32_k<double2><<<g, 256, 0, s>>>((const double2*)abi, (float4*)internal, V);
         else pack_gauge32_k<float2><<<g, 256, 0, s>>>((const float2*)abi, (float4*)internal, V);
@@ -708,7 +717,7 @@ void small_space_project(const void* V, int na, const double* d_signs, const voi
 #define OVL_INST(R)                                                                                                  \
     template void launch_pack_spinor<R>(const void*, int, void*, int, int, cudaStream_t);                           \
     template void launch_unpack_spinor<R>(const void*, void*, int, int, int, cudaStream_t);                         \
-    template void launch_pack_gauge<R>(const void*, int, void*, int, cudaStream_t);                                 \
+    template void launch_pack_gauge<R>(const void*, int, void*, const Geom&, cudaStream_t);                                 \
     template void dot_rhs<R>(const void*, const void*, long long, int, double2*, double2*, double2*, cudaStream_t); \
     template void norm2_rhs<R>(const void*, long long, int, double*, double2*, double2*, cudaStream_t);             \
     template void launch_axpby<R>(const double*, const void*, const double*, void*, long long, int, cudaStream_t);  \

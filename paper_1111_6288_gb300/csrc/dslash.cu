@@ -49,6 +49,19 @@ template <typename R>
 __device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
     return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
+// a * b + c, one rounding (explicit so that every complex multiply-add is four FMAs)
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+// a * b + z
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma(Cx<R> a, Cx<R> b, Cx<R> z) {
+    return {fmar(a.re, b.re, fmar(-a.im, b.im, z.re)), fmar(a.re, b.im, fmar(a.im, b.re, z.im))};
+}
+// conj(a) * b + z
+template <typename R>
+__device__ __forceinline__ Cx<R> cfmac(Cx<R> a, Cx<R> b, Cx<R> z) {
+    return {fmar(a.re, b.re, fmar(a.im, b.im, z.re)), fmar(a.re, b.im, fmar(-a.im, b.re, z.im))};
+}
 template <typename R>
 __device__ __forceinline__ Cx<R> cscale(R s, Cx<R> a) { return {s * a.re, s * a.im}; }
 template <typename R>
@@ -175,11 +188,16 @@ struct Args {
     int g5;
 };
 
+// How a hop's product is scaled: not at all (factor 1, or a boundary sign that the FP64 links
+// carry), by a real boundary factor (FP32 links cannot carry a sign: their third row is
+// rebuilt from the first two), or by a complex factor (the field phase on x hops).
+enum { kNoFac = 0, kRealFac = 1, kCplxFac = 2 };
+
 // Accumulate one hop in direction MU: forward (FWD) uses U_mu(n) psi(n+mu) with
 // (1 - gamma_mu); backward uses U_mu(n-mu)^+ psi(n-mu) with (1 + gamma_mu).
-template <typename R, int MU, bool FWD>
+template <typename R, int MU, bool FWD, int KIND>
 __device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, int link_site, Cx<R> fac,
-                                    bool complex_fac, Cx<R> (&acc)[12]) {
+                                    Cx<R> (&acc)[12]) {
     constexpr int S = FWD ? 2 : 0;  // forward: h = psi_up - G psi_dn (multiply G by -1)
     using G = GBlock<MU>;
     const long long V = a.V;
@@ -203,13 +221,19 @@ __device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, in
     for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            Cx<R> z = {0, 0};
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if constexpr (FWD) z = cadd(z, cmul(u[i][j], h[s][j]));   // U h
-                else z = cadd(z, cmulc(u[j][i], h[s][j]));               // U^+ h
+            Cx<R> z;
+            if constexpr (FWD) {  // U h
+                z = cmul(u[i][0], h[s][0]);
+                z = cfma(u[i][1], h[s][1], z);
+                z = cfma(u[i][2], h[s][2], z);
+            } else {  // U^+ h
+                z = cmulc(u[0][i], h[s][0]);
+                z = cfmac(u[1][i], h[s][1], z);
+                z = cfmac(u[2][i], h[s][2], z);
             }
-            w[s][i] = complex_fac ? cmul(fac, z) : cscale(fac.re, z);
+            if constexpr (KIND == kCplxFac) w[s][i] = cmul(fac, z);
+            else if constexpr (KIND == kRealFac) w[s][i] = cscale(fac.re, z);
+            else w[s][i] = z;
         }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -226,49 +250,80 @@ __device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, in
     }
 }
 
-template <typename R, int MU>
+// Both hops of direction MU.  XCPLX: the x hops carry the complex factor ph (forward) and
+// conj(ph) (backward).  FP64 links carry the boundary signs (folded in when they are packed),
+// so FP64 hops are scaled only by a phase; Dirichlet hops are skipped in both precisions.
+template <typename R, int MU, bool XCPLX>
 __device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int s, int xmu, Cx<R> ph,
                                           Cx<R> (&acc)[12]) {
+    constexpr bool FOLD = sizeof(R) == sizeof(double);
     const int L = a.L[MU], st = a.stride[MU];
     // forward neighbour
     {
-        int nb = (xmu == L - 1) ? s - (L - 1) * st : s + st;
-        R f = (xmu == L - 1) ? a.bcf[MU] : R(1);
+        const bool edge = xmu == L - 1;
+        const int nb = edge ? s - (L - 1) * st : s + st;
+        const R f = edge ? a.bcf[MU] : R(1);
         if (f != R(0)) {
-            if (MU == 0) hop<R, MU, true>(a, in, nb, s, {f * ph.re, f * ph.im}, true, acc);
-            else hop<R, MU, true>(a, in, nb, s, {f, R(0)}, false, acc);
+            if constexpr (MU == 0 && XCPLX)
+                hop<R, MU, true, kCplxFac>(a, in, nb, s, FOLD ? ph : Cx<R>{f * ph.re, f * ph.im}, acc);
+            else if constexpr (FOLD) hop<R, MU, true, kNoFac>(a, in, nb, s, {f, R(0)}, acc);
+            else hop<R, MU, true, kRealFac>(a, in, nb, s, {f, R(0)}, acc);
         }
     }
     // backward neighbour
     {
-        int nb = (xmu == 0) ? s + (L - 1) * st : s - st;
-        R f = (xmu == 0) ? a.bcf[MU] : R(1);
+        const bool edge = xmu == 0;
+        const int nb = edge ? s + (L - 1) * st : s - st;
+        const R f = edge ? a.bcf[MU] : R(1);
         if (f != R(0)) {
-            if (MU == 0) hop<R, MU, false>(a, in, nb, nb, {f * ph.re, -f * ph.im}, true, acc);
-            else hop<R, MU, false>(a, in, nb, nb, {f, R(0)}, false, acc);
+            if constexpr (MU == 0 && XCPLX)
+                hop<R, MU, false, kCplxFac>(a, in, nb, nb, FOLD ? Cx<R>{ph.re, -ph.im} : Cx<R>{f * ph.re, -f * ph.im},
+                                            acc);
+            else if constexpr (FOLD) hop<R, MU, false, kNoFac>(a, in, nb, nb, {f, R(0)}, acc);
+            else hop<R, MU, false, kRealFac>(a, in, nb, nb, {f, R(0)}, acc);
         }
     }
 }
 
 // Block = DSLASH_THREADS threads = (DSLASH_THREADS / b sites) x (b right-hand sides), b in
-// {1, 2, 4} (the caller's rhs_block, autotuned by the library; default 1 for one
+// {1, 2, 4} (the low bits of the caller's launch shape, autotuned by the library; default 1 for one
 // right-hand side, else 2), so that the threads of one site share the SM's L1 for the
-// site's links.  DSLASH_MIN_BLOCKS bounds the registers per thread.
+// site's links.
 #ifndef OVL_DSLASH_THREADS
 #define OVL_DSLASH_THREADS 128
 #endif
-#ifndef OVL_DSLASH_MIN_BLOCKS
-#define OVL_DSLASH_MIN_BLOCKS 1
+#ifndef OVL_DSLASH_MIN_BLOCKS_F32
+#define OVL_DSLASH_MIN_BLOCKS_F32 6
+#endif
+#ifndef OVL_DSLASH_MIN_BLOCKS_F64
+#define OVL_DSLASH_MIN_BLOCKS_F64 1
 #endif
 
 constexpr int DSLASH_THREADS = OVL_DSLASH_THREADS;
+
+// Blocks per SM that the register allocation must allow.  FP32: 6 (80 registers, no
+// spills), 7-9 % faster than the unconstrained 87 registers at 16^3 x 32 and 24^3 x 48,
+// where more resident warps hide the latency of the neighbour loads; FP64 needs its
+// registers (a cap makes it spill).  The dense FP32 shape (kShapeDense) allows 7 (72
+// registers, a few bytes spilled): a grid of up to 7 x 152 blocks then runs in one wave,
+// which wins on a 16^3 x 32 lattice with one right-hand side (1024 blocks); the library
+// times both shapes per batch size and keeps the faster.
+template <typename R> struct MinBlocks;
+template <> struct MinBlocks<float> {
+    static constexpr int value = OVL_DSLASH_MIN_BLOCKS_F32;
+    static constexpr int dense = 7;
+};
+template <> struct MinBlocks<double> {
+    static constexpr int value = OVL_DSLASH_MIN_BLOCKS_F64;
+    static constexpr int dense = OVL_DSLASH_MIN_BLOCKS_F64;
+};
 
 // DERIV: instead of H_w, its derivative with respect to the field phase phi of the
 // right-hand side: only the x hops depend on phi, through exp(i phi t) U_x(n) (forward)
 // and exp(-i phi t) U_x(n-x)^+ (backward), whose derivatives bring the factors i t and
 // -i t; the mass term drops out.
-template <typename R, bool DERIV>
-__global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_kernel(Args<R> a, int nrhs) {
+template <typename R, bool DERIV, int MINB>
+__global__ void __launch_bounds__(DSLASH_THREADS, MINB) dslash_kernel(Args<R> a, int nrhs) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     if (s >= a.V || r >= nrhs) return;
@@ -285,9 +340,19 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
     const int x3 = t / a.L[2];
     Cx<R> ph = {R(1), R(0)};
     if (a.phase) {
-        double sn, cs;
-        sincos(a.phase[r] * (double)x3, &sn, &cs);
-        ph = {(R)cs, (R)sn};
+        // The angle phi t is formed in FP64 (one multiply); the FP32 kernel takes its sine and
+        // cosine in FP32 (absolute error ~1e-7, below the kernel's own rounding), which keeps the
+        // slow FP64 pipe of this GPU out of the single-precision path.
+        const double ang = a.phase[r] * (double)x3;
+        if constexpr (sizeof(R) == sizeof(float)) {
+            float sn, cs;
+            sincosf((float)ang, &sn, &cs);
+            ph = {cs, sn};
+        } else {
+            double sn, cs;
+            sincos(ang, &sn, &cs);
+            ph = {cs, sn};
+        }
     }
     const R cop = a.c_op, c1 = a.c1;
     const R c2 = a.c2r ? a.c2 * (R)a.c2r[(long long)r * a.c2r_stride] : a.c2;
@@ -295,27 +360,24 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
     Cx<R> z[12], tmp[12];
+    // z = c_op gamma5 (diag psi - acc / 2) = cd psi + ch acc on the upper spins, negated on the lower
+    const R cd = cop * a.diag, ch = R(-0.5) * cop;
     if constexpr (DERIV) {
         const R tt = (R)x3;
-        both_hops<R, 0>(a, in, s, x0, {-tt * ph.im, tt * ph.re}, acc);  // i t exp(i phi t)
+        both_hops<R, 0, true>(a, in, s, x0, {-tt * ph.im, tt * ph.re}, acc);  // i t exp(i phi t)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            Cx<R> d = cscale(R(-0.5), acc[k]);
-            if (k >= 6) d = {-d.re, -d.im};  // gamma5
-            z[k] = cscale(cop, d);
-        }
+        for (int k = 0; k < 12; ++k) z[k] = cscale(k < 6 ? ch : -ch, acc[k]);
     } else {
-        both_hops<R, 0>(a, in, s, x0, ph, acc);
-        both_hops<R, 1>(a, in, s, x1, ph, acc);
-        both_hops<R, 2>(a, in, s, x2, ph, acc);
-        both_hops<R, 3>(a, in, s, x3, ph, acc);
-        // z = c_op * gamma5 (diag psi - acc/2)
+        if (a.phase) both_hops<R, 0, true>(a, in, s, x0, ph, acc);
+        else both_hops<R, 0, false>(a, in, s, x0, ph, acc);
+        both_hops<R, 1, false>(a, in, s, x1, ph, acc);
+        both_hops<R, 2, false>(a, in, s, x2, ph, acc);
+        both_hops<R, 3, false>(a, in, s, x3, ph, acc);
         IO<R>::load(in, V, s, tmp);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            Cx<R> d = csub(cscale(a.diag, tmp[k]), cscale(R(0.5), acc[k]));
-            if (k >= 6) d = {-d.re, -d.im};  // gamma5
-            z[k] = cscale(cop, d);
+            const R sd = k < 6 ? cd : -cd, sh = k < 6 ? ch : -ch;
+            z[k] = {fmar(sd, tmp[k].re, sh * acc[k].re), fmar(sd, tmp[k].im, sh * acc[k].im)};
         }
     }
     // + c1 v1
@@ -358,7 +420,7 @@ __global__ void __launch_bounds__(DSLASH_THREADS, OVL_DSLASH_MIN_BLOCKS) dslash_
 
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
-                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv, int rhs_block) {
+                   const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv, int shape) {
     Args<R> a;
     a.U = links;
     a.in = in;
@@ -384,13 +446,20 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
     }
     a.V = g.V;
     a.g5 = e.g5;
-    int by = rhs_block > 0 ? rhs_block : (nrhs > 1 ? 2 : 1);
+    const bool dense = (shape & kShapeDense) != 0;
+    int by = (shape & kShapeRhsMask) > 0 ? (shape & kShapeRhsMask) : (nrhs > 1 ? 2 : 1);
     while (by > 1 && by > nrhs) by >>= 1;
     const int bx = DSLASH_THREADS / by;
     dim3 block(bx, by);
     dim3 grid((g.V + bx - 1) / bx, (nrhs + by - 1) / by);
-    if (deriv) dslash_kernel<R, true><<<grid, block, 0, s>>>(a, nrhs);
-    else dslash_kernel<R, false><<<grid, block, 0, s>>>(a, nrhs);
+    constexpr int mb = MinBlocks<R>::value, md = MinBlocks<R>::dense;
+    if (deriv) {
+        if (dense) dslash_kernel<R, true, md><<<grid, block, 0, s>>>(a, nrhs);
+        else dslash_kernel<R, true, mb><<<grid, block, 0, s>>>(a, nrhs);
+    } else {
+        if (dense) dslash_kernel<R, false, md><<<grid, block, 0, s>>>(a, nrhs);
+        else dslash_kernel<R, false, mb><<<grid, block, 0, s>>>(a, nrhs);
+    }
     count_launch();
 }
 

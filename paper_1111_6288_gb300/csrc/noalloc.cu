@@ -114,7 +114,7 @@ extern "C" int apply_wilson_noalloc(const int dims[4], const int bc[4], double m
         e = cudaMemcpyAsync(d_phase, phase, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return reject(OV_ERR_CUDA, "apply_wilson_noalloc: phase upload failed");
     }
-    ovl::launch_pack_gauge<double>(U, OV_C128, links, g.V, s);
+    ovl::launch_pack_gauge<double>(U, OV_C128, links, g, s);
     ovl::launch_pack_spinor<double>(in, OV_C128, xin, g.V, nrhs, s);
     ovl::Epilogue ep;
     ep.g5 = hermitian ? 0 : 1;  // gamma5 H_w = D_w

@@ -55,12 +55,15 @@ struct Epilogue {
 
 // ---- kernels: dslash.cu ---------------------------------------------------
 // deriv: apply dH_w/dphi (the phi-derivative of the x hops, per right-hand-side phase) in
-// place of H_w; the epilogue is the same.  rhs_block: right-hand sides per thread block
-// (1, 2 or 4; 0 = default).
+// place of H_w; the epilogue is the same.  shape: right-hand sides per thread block in the
+// low bits (1, 2 or 4; 0 = default), | kShapeDense for the FP32 kernel whose registers allow
+// 7 resident blocks per SM instead of 6 (no effect in FP64).
+constexpr int kShapeRhsMask = 7;
+constexpr int kShapeDense = 8;
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
                    const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv = false,
-                   int rhs_block = 0);
+                   int shape = 0);
 
 // ---- kernels: blas.cu -----------------------------------------------------
 // ABI spinor [rhs][site][12] (dtype_in: 0 complex128, 1 complex64) -> internal [rhs][12][V] of R.
@@ -68,9 +71,10 @@ template <typename R>
 void launch_pack_spinor(const void* abi, int dtype_in, void* internal, int V, int nrhs, cudaStream_t s);
 template <typename R>
 void launch_unpack_spinor(const void* internal, void* abi, int dtype_out, int V, int nrhs, cudaStream_t s);
-// ABI links [4][site][3][3] -> internal [4][9][V] of R.
+// ABI links [4][site][3][3] -> internal links of R (FP64: [4][9][V] with the antiperiodic
+// boundary signs of g folded in; FP32: [4][3][V] float4, rows 0 and 1).
 template <typename R>
-void launch_pack_gauge(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s);
+void launch_pack_gauge(const void* abi, int dtype_in, void* internal, const Geom& g, cudaStream_t s);
 // Conversion of nvec spinor vectors between precisions (and internal layouts).
 template <typename RI, typename RO>
 void launch_convert(const void* in, void* out, int V, long long nvec, cudaStream_t s);
