@@ -48,10 +48,10 @@ BC = (0, 0, 0, 1)  # periodic x, y, z; antiperiodic t
 METRIC = "D_ov applies/s, dslash HBM GB/s, time-to-1e-10 solve (mixed vs FP64)"
 UNIT = "D_ov applies/s"
 WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV}, m={MASS}, tol={TOL}"
-# ncu: DRAM bytes of the FP32 Wilson kernel over its algorithmic bytes (plain and Clenshaw-epilogue
-# launches, 24^3x48 capture); None until the current kernel has been captured.  Update together
-# with profiles/ whenever the kernel changes.
-DRAM_OVER_ALGORITHMIC = None
+# ncu: DRAM bytes of the FP32 Wilson kernel over its algorithmic bytes on the bench lattice with warm
+# caches (plain and Clenshaw-epilogue launches, profiles/dslash_f32_16x16x16x32_warm_l2.md): the
+# loop's vectors and links stay in L2.  Set to None whenever the kernel changes until re-measured.
+DRAM_OVER_ALGORITHMIC = 0.32
 
 
 def dist_env():
@@ -215,19 +215,23 @@ def run_reference(args):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_case(dims):
-    """A few FP32 Wilson-kernel launches (plain and Clenshaw-epilogue) on one lattice."""
+def kernel_case(dims, precision="f32"):
+    """A few Wilson-kernel launches (plain and Clenshaw-epilogue) on one lattice.
+
+    FP32: the first 12 launches time the two launch shapes, then the Clenshaw steps follow
+    (plain, epilogue, ...).  FP64 has one shape and no timing launches."""
     import torch
 
     import paper_1111_6288_gb300 as P
     import synth
 
+    prec = P.OV_PREC_F32 if precision == "f32" else P.OV_PREC_F64
     U = torch.from_numpy(synth.random_su3_field(dims, LINK_EPS, 0)).cuda()
-    ctx = P.Context(P.Params(dims=dims, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=4, precision=P.OV_PREC_F32,
-                             inner_precision=P.OV_PREC_F32, max_nrhs=1))
+    ctx = P.Context(P.Params(dims=dims, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=4, precision=prec,
+                             inner_precision=prec, max_nrhs=1))
     ctx.set_gauge(U)
     del U
-    x = torch.from_numpy(synth.gaussian_spinor(dims, 1, 1)).to(torch.complex64).cuda()
+    x = torch.from_numpy(synth.gaussian_spinor(dims, 1, 1)).to(ctx.spinor_dtype()).cuda()
     y = torch.empty_like(x)
     for _ in range(2):
         P.apply_overlap(ctx, x, y, mass=MASS)
@@ -247,6 +251,7 @@ def main():
                     help="profiling case: a few FP32 Wilson-kernel launches (default 24^3x48), "
                          "then exit without a JSON line")
     ap.add_argument("--kernel-dims", default="24,24,24,48", help="lattice of the profiling case: Lx,Ly,Lz,Lt")
+    ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"], help="precision of the profiling case")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -255,7 +260,7 @@ def main():
         run_reference(args)
         return
     if args.kernel_case:
-        kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")))
+        kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision)
         return
 
     import numpy as np
@@ -289,6 +294,12 @@ def main():
     t_eig = time.perf_counter() - t0
     eig_info = ctx_64.last_info
     P.deflate(ctx_mix, V, lam)
+    # 16-bit storage of links and recurrence vectors (FP32 arithmetic): isolated D(m) rate and error
+    ctx_half = {}
+    for name, prec in (("f16", P.OV_PREC_F16), ("bf16", P.OV_PREC_BF16)):
+        ctx_half[name] = P.Context(P.Params(precision=prec, inner_precision=P.OV_PREC_F32, **common))
+        ctx_half[name].set_gauge(U)
+        P.deflate(ctx_half[name], V, lam)
     del V
     # replicas solve different spin-colour point sources
     sc = (rank % 4, (rank // 4) % 3)
@@ -369,6 +380,20 @@ def main():
 
     rate32 = dov_rate(ctx_mix, 5)
     rate64 = dov_rate(ctx_64, 2)
+    rates_half = {name: dov_rate(c, 5) for name, c in ctx_half.items()}
+
+    # error of one D(m) application on a Gaussian vector against the FP64 path (max |diff| / max |FP64|)
+    xg = torch.from_numpy(synth.gaussian_spinor(DIMS, 1, 7)).to(dev)
+    y64 = torch.empty_like(xg)
+    P.apply_overlap(ctx_64, xg, y64, mass=MASS)
+    errors = {}
+    for name, c in [("f32", ctx_mix)] + list(ctx_half.items()):
+        x32 = xg.to(torch.complex64)
+        y = torch.empty_like(x32)
+        P.apply_overlap(c, x32, y, mass=MASS)
+        errors[name] = float((y.to(torch.complex128) - y64).abs().max() / y64.abs().max())
+    for c in ctx_half.values():
+        c.close()
 
     # ---- FP64-only solve (time-to-solution comparison) ----
     fp64 = None
@@ -390,8 +415,8 @@ def main():
     achieved = prof32["clenshaw_bytes"] / (prof32["clenshaw_ms"] / 1e3) / 1e9 if prof32["clenshaw_ms"] > 0 else 0.0
     bytes_per_launch = prof32["clenshaw_bytes"] / max(prof32["clenshaw_launches"], 1)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                # DRAM bytes per launch: ncu dram__bytes_read + write of this kernel measured 0.965 of its
-                # algorithmic bytes (profiles/dslash_f32_24x24x24x48_ncu_full.md), scaled to this launch mix
+                # DRAM bytes per launch: ncu's DRAM bytes of this kernel on this lattice over its algorithmic
+                # bytes, scaled to this launch mix
                 "traffic": DRAM_OVER_ALGORITHMIC * bytes_per_launch if DRAM_OVER_ALGORITHMIC else None,
                 "traffic_unit": "B/launch",
                 "peak_source": peak_kind,
@@ -422,7 +447,8 @@ def main():
                                  "mixed_outer_iters": stats[0].outer_iters, "mixed_inner_iters": stats[0].inner_iters,
                                  "mixed_sign_applies": stats[0].sign_applies,
                                  "mixed_true_residual": worst_res, "fp64": fp64},
-            "dov_apply_per_s": {"f32": rate32, "f64": rate64},
+            "dov_apply_per_s": {"f32": rate32, "f64": rate64, **rates_half},
+            "dov_error_vs_f64": errors,
             "dslash_gbs": achieved,
             "roofline": roofline,
             "clocks": clk,

@@ -71,8 +71,14 @@ enum {
 enum { OV_BC_PERIODIC = 0, OV_BC_ANTIPERIODIC = 1, OV_BC_DIRICHLET = 2 };
 
 /* Arithmetic of operator applications. F64: FP64 storage and arithmetic.
- * F32: FP32 storage and arithmetic (reductions accumulate in FP64). */
-enum { OV_PREC_F64 = 0, OV_PREC_F32 = 1 };
+ * F32: FP32 storage and arithmetic (reductions accumulate in FP64).
+ * F16, BF16 (precision only, not inner_precision): the gauge links and the vectors of the
+ * Chebyshev recurrence are stored in 16 bits (FP16 with one FP32 scale per site, or BF16)
+ * and computed in FP32; the small-space projection, the final application of H_w and the
+ * caller arrays (complex64) stay FP32.  The result carries the 16-bit rounding (relative
+ * error ~1e-3 for FP16, ~1e-2 for BF16), which the solver's defect correction cannot absorb
+ * at light quark masses, so solve_overlap keeps FP32 or FP64 in its inner loop. */
+enum { OV_PREC_F64 = 0, OV_PREC_F32 = 1, OV_PREC_F16 = 2, OV_PREC_BF16 = 3 };
 
 /* Element type of caller arrays. */
 enum { OV_C128 = 0, OV_C64 = 1 };
@@ -141,8 +147,8 @@ double ov_poly_delta(const ov_ctx* ctx);
 
 /* Turn event timing of the polynomial loops on (on != 0) or off. */
 int ov_set_profiling(ov_ctx* ctx, int on);
-/* Synchronise the events recorded for loops of the given precision (OV_PREC_*), sum them
- * into *out and reset that record. */
+/* Synchronise the events recorded for loops whose recurrence is stored in the given precision
+ * (OV_PREC_*), sum them into *out and reset that record. */
 int ov_read_profile(ov_ctx* ctx, int precision, ov_profile* out);
 /* Kernels launched by the library so far (all contexts). */
 long long ov_launch_count(void);
@@ -166,7 +172,8 @@ int ov_host_eigh(int n, double* A, double* w, double* Z);
 
 /* out = D_w in (hermitian = 0) or H_w in = gamma5 D_w in (hermitian = 1).
  * in, out: device spinors [nrhs][site][4][3], dtype OV_C128 if ctx precision is F64,
- * OV_C64 if F32; in != out.  phase: host [nrhs] phi_j = q_j E_j (NULL = all zero). */
+ * OV_C64 otherwise (F16 / BF16: in is rounded to 16 bits, the result read back into FP32);
+ * in != out.  phase: host [nrhs] phi_j = q_j E_j (NULL = all zero). */
 int apply_wilson(ov_ctx* ctx, const void* in, void* out, int nrhs, const double* phase,
                  int hermitian, ov_stream_t stream);
 

@@ -16,6 +16,8 @@ from ._ovl import (  # noqa: F401
     OV_BC_ANTIPERIODIC,
     OV_BC_DIRICHLET,
     OV_BC_PERIODIC,
+    OV_PREC_BF16,
+    OV_PREC_F16,
     OV_PREC_F32,
     OV_PREC_F64,
     Context,

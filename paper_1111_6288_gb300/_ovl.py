@@ -13,7 +13,7 @@ _LIB_PATH = os.path.join(HERE, "libovl.so")
 
 OV_OK = 0
 OV_BC_PERIODIC, OV_BC_ANTIPERIODIC, OV_BC_DIRICHLET = 0, 1, 2
-OV_PREC_F64, OV_PREC_F32 = 0, 1
+OV_PREC_F64, OV_PREC_F32, OV_PREC_F16, OV_PREC_BF16 = 0, 1, 2, 3
 OV_C128, OV_C64 = 0, 1
 ERROR_NAMES = {1: "ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN", 6: "NAN", 7: "TIMEOUT",
                8: "NO_BANK", 9: "STATE"}

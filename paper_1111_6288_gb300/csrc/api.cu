@@ -61,6 +61,7 @@ struct ov_ctx {
     std::string info;  // summary of the last eigensolver / solve call
     void* U64 = nullptr;
     void* U32 = nullptr;
+    void* U16 = nullptr;  // 16-bit links of an FP16 / BF16 context
     bool gauge_set = false;
     std::vector<Bank> banks;
     std::map<std::string, Buf> ws;
@@ -85,9 +86,9 @@ struct ov_ctx {
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, std::pair<cudaGraphExec_t, void*>> graphs;  // exec, buffer holding p
     bool profile = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[2];  // per OV_PREC_*
-    long long prof_launches[2] = {0, 0};
-    double prof_bytes[2] = {0.0, 0.0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[4];  // per OV_PREC_* of the recurrence
+    long long prof_launches[4] = {0, 0, 0, 0};
+    double prof_bytes[4] = {0.0, 0.0, 0.0, 0.0};
 };
 
 namespace {
@@ -123,14 +124,28 @@ int fail(ov_ctx* c, int code, const char* fmt, ...) {
     } while (0)
 
 template <typename R>
-constexpr int prec_of() { return std::is_same<R, double>::value ? OV_PREC_F64 : OV_PREC_F32; }
+constexpr int prec_of() {
+    return std::is_same<R, double>::value ? OV_PREC_F64
+           : std::is_same<R, float>::value ? OV_PREC_F32
+           : std::is_same<R, H16>::value   ? OV_PREC_F16
+                                           : OV_PREC_BF16;
+}
 
-size_t vec_bytes(const ov_ctx* c, int prec) { return (size_t)12 * c->g.V * (prec == OV_PREC_F64 ? 16 : 8); }
+// bytes of one spinor vector, and of one site's spinor and links, per precision
+size_t vec_bytes(const ov_ctx* c, int prec) {
+    if (prec == OV_PREC_F16) return (size_t)half_rhs_bytes<H16>(c->g.V);
+    if (prec == OV_PREC_BF16) return (size_t)half_rhs_bytes<B16>(c->g.V);
+    return (size_t)12 * c->g.V * (prec == OV_PREC_F64 ? 16 : 8);
+}
+double site_spinor_bytes(int prec) { return prec == OV_PREC_F64 ? 192 : prec == OV_PREC_F32 ? 96 : prec == OV_PREC_F16 ? 52 : 48; }
+double site_link_bytes(int prec) { return prec == OV_PREC_F64 ? 576 : prec == OV_PREC_F32 ? 192 : 96; }
+
 
 // Named workspace of at least nvec spinor vectors of the given precision.
 int workspace(ov_ctx* c, const std::string& name, int prec, long long nvec, void** out) {
     const size_t need = vec_bytes(c, prec) * (size_t)std::max<long long>(nvec, 1);
-    const std::string key = name + (prec == OV_PREC_F64 ? "/64" : "/32");
+    static const char* suffix[4] = {"/64", "/32", "/16", "/b16"};
+    const std::string key = name + suffix[prec];
     Buf& b = c->ws[key];
     if (b.bytes < need) {
         if (b.ptr) {
@@ -185,6 +200,14 @@ int ensure_small(ov_ctx* c, long long nmat, long long npartial, int nsys) {
         CK(cudaMalloc(&c->d_red, sizeof(double2) * c->cap_sys));
     }
     return OV_OK;
+}
+
+// links stored for storage type S
+template <typename S>
+const void* links_of(const ov_ctx* c) {
+    if constexpr (std::is_same<S, double>::value) return c->U64;
+    else if constexpr (std::is_same<S, float>::value) return c->U32;
+    else return c->U16;
 }
 
 Bank* find_bank(ov_ctx* c, double phase) {
@@ -253,9 +276,9 @@ bool any_phase(const SysSet& S) {
     return false;
 }
 
-// Launch shape of the Wilson kernel for ns systems of precision R (right-hand sides per block,
-// and in FP32 the 6- or 7-blocks-per-SM register budget): timed once on the sign pipeline's own
-// buffers (the Clenshaw-step launch with its epilogue), fastest kept.
+// Launch shape of the Wilson kernel for ns systems of storage type R (right-hand sides per block,
+// and for FP32 arithmetic the 6- or 7-blocks-per-SM register budget): timed once on the sign
+// pipeline's own buffers (the Clenshaw-step launch with its epilogue), fastest kept.
 template <typename R>
 int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* in, void* v1, void* v2,
                 void* v3, void* out, cudaStream_t s) {
@@ -266,7 +289,7 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
     for (int by : {1, 2, 4}) {
         if (by > ns) break;
         shapes.push_back(by);
-        if (std::is_same<R, float>::value) shapes.push_back(by | kShapeDense);
+        if (!std::is_same<R, double>::value) shapes.push_back(by | kShapeDense);
     }
     int best = shapes[0];
     if (shapes.size() > 1) {
@@ -309,9 +332,14 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
 
 // out = Proj(G(c_op H_w P(Q^2) x_perp + c1 y_s)) + c2 v2 + c3 v3 over S.n systems of precision R,
 // where (y_s, x_perp) is the projection of (g5_in ? gamma5 X : X).  fin.v1 is set here.
-template <typename R>
+// ST: storage of the links and vectors of the recurrence: R itself, or (R = float) a 16-bit
+// format, x_perp then being rounded to it and P(Q^2) x_perp read back into FP32 for the final
+// FP32 application of H_w.
+template <typename R, typename ST = R>
 int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogue fin, void* out, cudaStream_t s) {
+    constexpr bool HALF = !std::is_same<R, ST>::value;
     const int prec = prec_of<R>();
+    const int precs = prec_of<ST>();
     const int V = c->g.V;
     const long long n12 = 12LL * V;
     const int ns = S.n;
@@ -322,9 +350,14 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     TRY(workspace(c, "sp_xg", prec, ns, &xg));
     TRY(workspace(c, "sp_xperp", prec, ns, &xperp));
     TRY(workspace(c, "sp_ys", prec, ns, &ys));
-    TRY(workspace(c, "sp_t", prec, ns, &t));
-    TRY(workspace(c, "sp_bA", prec, ns, &bA));
-    TRY(workspace(c, "sp_bB", prec, ns, &bB));
+    TRY(workspace(c, "sp_t", precs, ns, &t));
+    TRY(workspace(c, "sp_bA", precs, ns, &bA));
+    TRY(workspace(c, "sp_bB", precs, ns, &bB));
+    void *xs = xperp, *p32 = nullptr;  // x_perp in the recurrence's storage; FP32 copy of its result
+    if (HALF) {
+        TRY(workspace(c, "sp_xs", precs, ns, &xs));
+        TRY(workspace(c, "sp_p32", prec, ns, &p32));
+    }
     const size_t es = sizeof(typename C2<R>::T);
 
     const void* src = X;
@@ -370,32 +403,38 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     const double alpha = 4.0 / ((1.0 - eps) * h * h);
     const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
     const double m0 = c->p.m0;
-    const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
+    const void* U = links_of<R>(c);
+    const void* Us = links_of<ST>(c);
     // algorithmic bytes per site of one launch: links once (shared by the systems) plus each
     // system's input, output and epilogue vectors
-    const double esd = (double)sizeof(typename C2<R>::T), Vd = (double)V;
-    const double link_cplx = std::is_same<R, double>::value ? 36.0 : 24.0;
+    const double Vd = (double)V, lb = site_link_bytes(precs), sb = site_spinor_bytes(precs);
     // the whole recurrence (2n launches, no host work) as one stream sequence
     // timing launches read t, bA, x_perp and write bB only (rewritten by the recurrence below)
-    const int rb = tuned_shape<R>(c, ns, U, d_phase, t, bA, xperp, bA, bB, s);
+    const int rb = tuned_shape<ST>(c, ns, Us, d_phase, t, bA, xs, bA, bB, s);
+    const int nconv = HALF ? 2 : 1;  // launches before the recurrence
     auto enqueue = [&](cudaStream_t st) -> void* {
-        launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, st);
+        if constexpr (HALF) {
+            launch_to_half<ST>(xperp, xs, V, ns, 1.0, st);
+            launch_to_half<ST>(xperp, bA, V, ns, c->coeffs[n], st);
+        } else {
+            launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, st);
+        }
         void* b1 = bA;
         void* b2 = nullptr;
         Epilogue plain;
         for (int k = n - 1; k >= 0; --k) {
-            launch_dslash<R>(c->g, m0, U, b1, t, ns, d_phase, plain, st, false, rb);
+            launch_dslash<ST>(c->g, m0, Us, b1, t, ns, d_phase, plain, st, false, rb);
             Epilogue e;
             const double half = (k == 0) ? 0.5 : 1.0;
             e.c_op = alpha * half;
             e.c1 = beta * half;
             e.v1 = b1;
             e.c2 = c->coeffs[k];
-            e.v2 = xperp;
+            e.v2 = xs;
             e.c3 = -1.0;
             e.v3 = b2;
             void* o = b2 ? b2 : bB;
-            launch_dslash<R>(c->g, m0, U, t, o, ns, d_phase, e, st, false, rb);
+            launch_dslash<ST>(c->g, m0, Us, t, o, ns, d_phase, e, st, false, rb);
             b2 = b1;
             b1 = o;
         }
@@ -407,16 +446,16 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
         CK(cudaEventCreate(&ev1));
         CK(cudaEventRecord(ev0, s));
         for (int k = n - 1; k >= 0; --k) {
-            c->prof_bytes[prec] += Vd * esd * (link_cplx + 24.0 * ns);                                  // t = H_w b1
-            c->prof_bytes[prec] += Vd * esd * (link_cplx + 12.0 * ns * (k == n - 1 ? 4.0 : 5.0));     // b_k
+            c->prof_bytes[precs] += Vd * (lb + 2.0 * ns * sb);                          // t = H_w b1
+            c->prof_bytes[precs] += Vd * (lb + ns * sb * (k == n - 1 ? 4.0 : 5.0));     // b_k
         }
-        c->prof_launches[prec] += 2LL * n;
+        c->prof_launches[precs] += 2LL * n;
     }
     void* b1 = nullptr;
     if (c->use_graphs) {
         char key[256];
-        snprintf(key, sizeof(key), "%d/%d/%d/%p/%p/%p/%p/%p/%p", prec, ns, rb, xperp, bA, bB, t, (const void*)d_phase,
-                 U);
+        snprintf(key, sizeof(key), "%d/%d/%d/%p/%p/%p/%p/%p/%p/%p", precs, ns, rb, xperp, xs, bA, bB, t,
+                 (const void*)d_phase, Us);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -431,10 +470,10 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
             cudaGraphDestroy(graph);
             if (e2 != cudaSuccess) return fail(c, OV_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
             it = c->graphs.emplace(key, std::make_pair(exec, res)).first;
-            g_launches.fetch_sub(2LL * n + 1);  // counted at replay, not at capture
+            g_launches.fetch_sub(2LL * n + nconv);  // counted at replay, not at capture
         }
         CK(cudaGraphLaunch(it->second.first, s));
-        count_launch(2LL * n + 1);
+        count_launch(2LL * n + nconv);
         b1 = it->second.second;
     } else {
         b1 = enqueue(s);
@@ -442,9 +481,13 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     CKL();
     if (c->profile) {
         CK(cudaEventRecord(ev1, s));
-        c->prof_events[prec].emplace_back(ev0, ev1);
+        c->prof_events[precs].emplace_back(ev0, ev1);
     }
     // b1 now holds p.  Final: out = Proj(G(c_op H_w p + c1 y_s)) + c2 v2 + c3 v3
+    if constexpr (HALF) {
+        launch_from_half<ST>(b1, p32, V, ns, s);
+        b1 = p32;
+    }
     fin.v1 = any_bank ? ys : nullptr;
     launch_dslash<R>(c->g, m0, U, b1, out, ns, d_phase, fin, s);
     CKL();
@@ -454,7 +497,7 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
 }
 
 // D(m) X (g5_in = false) or D(m)^+ X (g5_in = true) on internal vectors.
-template <typename R>
+template <typename R, typename ST = R>
 int overlap_op(ov_ctx* c, const void* X, const SysSet& S, double mass, bool dagger, void* out, cudaStream_t s) {
     Epilogue fin;
     fin.c_op = (1.0 - 0.5 * mass) / c->hw_norm;
@@ -462,7 +505,7 @@ int overlap_op(ov_ctx* c, const void* X, const SysSet& S, double mass, bool dagg
     fin.g5 = dagger ? 0 : 1;
     fin.c2 = 1.0 + 0.5 * mass;
     fin.v2 = X;
-    return sign_pipeline<R>(c, X, S, dagger, fin, out, s);
+    return sign_pipeline<R, ST>(c, X, S, dagger, fin, out, s);
 }
 
 int check_ready(ov_ctx* c, const void* in, const void* out, int nrhs) {
@@ -490,7 +533,8 @@ int phase_check(ov_ctx* c, const SysSet& S) {
     return OV_OK;
 }
 
-template <typename R>
+// ST: storage of the links and vectors of the Wilson kernels (R, or a 16-bit format with R = float).
+template <typename R, typename ST = R>
 int apply_generic(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, int kind, double mass,
                   cudaStream_t s) {
     const int prec = prec_of<R>();
@@ -506,21 +550,40 @@ int apply_generic(ov_ctx* c, const void* in, void* out, int nrhs, const double* 
         TRY(upload_sys(c, S, s));
         Epilogue e;
         e.g5 = (kind == 0);  // gamma5 H_w = D_w
-        launch_dslash<R>(c->g, c->p.m0, std::is_same<R, double>::value ? c->U64 : c->U32, X, Y, nrhs,
-                         any_phase(S) ? c->d_phase : nullptr, e, s);
+        const double* d_phase = any_phase(S) ? c->d_phase : nullptr;
+        if constexpr (std::is_same<R, ST>::value) {
+            launch_dslash<R>(c->g, c->p.m0, links_of<R>(c), X, Y, nrhs, d_phase, e, s);
+        } else {  // input rounded to the 16-bit format, output read back into FP32
+            void *Xh, *Yh;
+            TRY(workspace(c, "io_in", prec_of<ST>(), nrhs, &Xh));
+            TRY(workspace(c, "io_out", prec_of<ST>(), nrhs, &Yh));
+            launch_to_half<ST>(X, Xh, c->g.V, nrhs, 1.0, s);
+            launch_dslash<ST>(c->g, c->p.m0, links_of<ST>(c), Xh, Yh, nrhs, d_phase, e, s);
+            launch_from_half<ST>(Yh, Y, c->g.V, nrhs, s);
+        }
         CKL();
         c->dslash_count += nrhs;
     } else if (kind == 2) {  // sign
         Epilogue fin;
         fin.c_op = 1.0 / c->hw_norm;
         fin.c1 = 1.0;
-        TRY(sign_pipeline<R>(c, X, S, false, fin, Y, s));
+        TRY((sign_pipeline<R, ST>(c, X, S, false, fin, Y, s)));
     } else {  // D(m)
-        TRY(overlap_op<R>(c, X, S, mass, false, Y, s));
+        TRY((overlap_op<R, ST>(c, X, S, mass, false, Y, s)));
     }
     launch_unpack_spinor<R>(Y, out, dt, c->g.V, nrhs, s);
     CKL();
     return OV_OK;
+}
+
+int apply_dispatch(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, int kind, double mass,
+                   cudaStream_t s) {
+    switch (c->p.precision) {
+        case OV_PREC_F64: return apply_generic<double>(c, in, out, nrhs, phase, kind, mass, s);
+        case OV_PREC_F32: return apply_generic<float>(c, in, out, nrhs, phase, kind, mass, s);
+        case OV_PREC_F16: return apply_generic<float, H16>(c, in, out, nrhs, phase, kind, mass, s);
+        default: return apply_generic<float, B16>(c, in, out, nrhs, phase, kind, mass, s);
+    }
 }
 
 // ---- block helpers for orthonormalisation and Rayleigh-Ritz (FP64) ----------------
@@ -753,10 +816,13 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     if (!(p->eps > 0.0 && p->eps < 1.0)) return fail(c, OV_ERR_ARG, "eps = %g outside (0, 1)", p->eps);
     if (p->poly_degree < 1 || p->poly_degree > 100000)
         return fail(c, OV_ERR_ARG, "poly_degree = %d outside [1, 100000]", p->poly_degree);
-    if (p->precision != OV_PREC_F64 && p->precision != OV_PREC_F32)
+    if (p->precision < OV_PREC_F64 || p->precision > OV_PREC_BF16)
         return fail(c, OV_ERR_ARG, "precision = %d invalid", p->precision);
     if (p->inner_precision != OV_PREC_F64 && p->inner_precision != OV_PREC_F32)
-        return fail(c, OV_ERR_ARG, "inner_precision = %d invalid", p->inner_precision);
+        return fail(c, OV_ERR_ARG,
+                    "inner_precision = %d invalid (the solver's inner loop runs in FP64 or FP32: 16-bit "
+                    "storage limits the operator to ~1e-3, too coarse for its defect correction)",
+                    p->inner_precision);
     if (p->max_nrhs < 1 || p->max_nrhs > kMaxRhs / 2)
         return fail(c, OV_ERR_ARG, "max_nrhs = %d outside [1, %d]", p->max_nrhs, kMaxRhs / 2);
     if (!std::isfinite(p->m0)) return fail(c, OV_ERR_ARG, "m0 not finite");
@@ -813,7 +879,7 @@ int ov_destroy(ov_ctx* c) {
             cudaEventDestroy(e.first);
             cudaEventDestroy(e.second);
         }
-    void* ps[] = {c->U64, c->U32, c->d_partial, c->d_red, c->d_C, c->d_C2, c->d_phase, c->d_chi, c->d_idx};
+    void* ps[] = {c->U64, c->U32, c->U16, c->d_partial, c->d_red, c->d_C, c->d_C2, c->d_phase, c->d_chi, c->d_idx};
     for (void* q : ps)
         if (q) cudaFree(q);
     delete c;
@@ -856,7 +922,7 @@ int ov_set_profiling(ov_ctx* c, int on) {
 }
 
 int ov_read_profile(ov_ctx* c, int precision, ov_profile* out) {
-    if (!c || !out || (precision != OV_PREC_F64 && precision != OV_PREC_F32)) return OV_ERR_ARG;
+    if (!c || !out || precision < OV_PREC_F64 || precision > OV_PREC_BF16) return OV_ERR_ARG;
     const int p = precision;
     double ms = 0.0;
     for (auto& e : c->prof_events[p]) {
@@ -886,15 +952,19 @@ int ov_set_gauge(ov_ctx* c, const void* U, int dtype, ov_stream_t stream) {
     if (dtype != OV_C128 && dtype != OV_C64) return fail(c, OV_ERR_ARG, "dtype = %d invalid", dtype);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = 4ull * 9 * c->g.V;
+    const bool half = c->p.precision == OV_PREC_F16 || c->p.precision == OV_PREC_BF16;
     if (!c->U64) {
         if (cudaMalloc(&c->U64, n * sizeof(double2)) != cudaSuccess ||
-            cudaMalloc(&c->U32, 4ull * 3 * c->g.V * sizeof(float4)) != cudaSuccess) {
+            cudaMalloc(&c->U32, 4ull * 3 * c->g.V * sizeof(float4)) != cudaSuccess ||
+            (half && cudaMalloc(&c->U16, 96ull * c->g.V) != cudaSuccess)) {
             cudaGetLastError();
             return fail(c, OV_ERR_OOM, "gauge field allocation failed");
         }
     }
     launch_pack_gauge<double>(U, dtype, c->U64, c->g, s);
     launch_pack_gauge<float>(U, dtype, c->U32, c->g, s);
+    if (c->p.precision == OV_PREC_F16) launch_pack_gauge_half<H16>(U, dtype, c->U16, c->g.V, s);
+    if (c->p.precision == OV_PREC_BF16) launch_pack_gauge_half<B16>(U, dtype, c->U16, c->g.V, s);
     CKL();
     c->gauge_set = true;
     return OV_OK;
@@ -904,16 +974,13 @@ int apply_wilson(ov_ctx* c, const void* in, void* out, int nrhs, const double* p
                  ov_stream_t stream) {
     TRY(check_ready(c, in, out, nrhs));
     cudaStream_t s = (cudaStream_t)stream;
-    const int kind = hermitian ? 1 : 0;
-    return c->p.precision == OV_PREC_F64 ? apply_generic<double>(c, in, out, nrhs, phase, kind, 0.0, s)
-                                         : apply_generic<float>(c, in, out, nrhs, phase, kind, 0.0, s);
+    return apply_dispatch(c, in, out, nrhs, phase, hermitian ? 1 : 0, 0.0, s);
 }
 
 int apply_sign_Hw(ov_ctx* c, const void* in, void* out, int nrhs, const double* phase, ov_stream_t stream) {
     TRY(check_ready(c, in, out, nrhs));
     cudaStream_t s = (cudaStream_t)stream;
-    return c->p.precision == OV_PREC_F64 ? apply_generic<double>(c, in, out, nrhs, phase, 2, 0.0, s)
-                                         : apply_generic<float>(c, in, out, nrhs, phase, 2, 0.0, s);
+    return apply_dispatch(c, in, out, nrhs, phase, 2, 0.0, s);
 }
 
 int apply_overlap(ov_ctx* c, const void* in, void* out, int nrhs, double mass, const double* phase,
@@ -921,8 +988,7 @@ int apply_overlap(ov_ctx* c, const void* in, void* out, int nrhs, double mass, c
     TRY(check_ready(c, in, out, nrhs));
     if (!std::isfinite(mass)) return fail(c, OV_ERR_ARG, "mass not finite");
     cudaStream_t s = (cudaStream_t)stream;
-    return c->p.precision == OV_PREC_F64 ? apply_generic<double>(c, in, out, nrhs, phase, 3, mass, s)
-                                         : apply_generic<float>(c, in, out, nrhs, phase, 3, mass, s);
+    return apply_dispatch(c, in, out, nrhs, phase, 3, mass, s);
 }
 
 int deflate(ov_ctx* c, double phase, const void* V, const double* lambda, int n_ev, int dtype, ov_stream_t stream) {

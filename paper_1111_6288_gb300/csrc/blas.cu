@@ -176,6 +176,46 @@ __global__ void convert_k(const void* __restrict__ in, void* __restrict__ out, i
     }
 }
 
+// FP32 spinors -> 16-bit storage (times factor) and back (half_store.h formats).
+template <typename S>
+__global__ void to_half_k(const void* __restrict__ in, void* __restrict__ out, int V, long long nvec, float factor) {
+    const long long total = (long long)V * nvec;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / V, s = i % V;
+        float2 p[12];
+        SiteIO<float>::load((const char*)in + r * 96 * V, V, s, p);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k] = make_float2(factor * p[k].x, factor * p[k].y);
+        half_store_site<S>((char*)out + r * half_rhs_bytes<S>(V), V, s, p);
+    }
+}
+
+template <typename S>
+__global__ void from_half_k(const void* __restrict__ in, void* __restrict__ out, int V, long long nvec) {
+    const long long total = (long long)V * nvec;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / V, s = i % V;
+        float2 p[12];
+        half_load_site<S, false>((const char*)in + r * half_rhs_bytes<S>(V), V, s, p);
+        SiteIO<float>::store((char*)out + r * 96 * V, V, s, p);
+    }
+}
+
+// ABI links -> rows 0 and 1 in 16-bit storage.  The boundary factors are applied by the hops.
+template <typename TI, typename S>
+__global__ void pack_gauge_half_k(const TI* __restrict__ abi, void* __restrict__ out, int V) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4LL * V) return;
+    const int mu = (int)(idx / V), s = (int)(idx % V);
+    const TI* src = abi + ((long long)mu * V + s) * 9;
+    float2 r[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r[k] = make_float2((float)src[k].x, (float)src[k].y);
+    half_store_link<S>(out, V, mu, s, r);
+}
+
 // ---- reductions ------------------------------------------------------------
 
 constexpr int RT = 256;
@@ -570,6 +610,33 @@ void launch_convert(const void* in, void* out, int V, long long nvec, cudaStream
     convert_k<RI, RO><<<grid_for((long long)V * nvec, 256), 256, 0, s>>>(in, out, V, nvec);
     count_launch();
 }
+
+template <typename S>
+void launch_to_half(const void* in32, void* out, int V, long long nvec, double factor, cudaStream_t s) {
+    to_half_k<S><<<grid_for((long long)V * nvec, 256), 256, 0, s>>>(in32, out, V, nvec, (float)factor);
+    count_launch();
+}
+
+template <typename S>
+void launch_from_half(const void* in, void* out32, int V, long long nvec, cudaStream_t s) {
+    from_half_k<S><<<grid_for((long long)V * nvec, 256), 256, 0, s>>>(in, out32, V, nvec);
+    count_launch();
+}
+
+template <typename S>
+void launch_pack_gauge_half(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s) {
+    const int g = (int)((4LL * V + 255) / 256);
+    if (dtype_in == 0) pack_gauge_half_k<double2, S><<<g, 256, 0, s>>>((const double2*)abi, internal, V);
+    else pack_gauge_half_k<float2, S><<<g, 256, 0, s>>>((const float2*)abi, internal, V);
+    count_launch();
+}
+
+template void launch_to_half<H16>(const void*, void*, int, long long, double, cudaStream_t);
+template void launch_to_half<B16>(const void*, void*, int, long long, double, cudaStream_t);
+template void launch_from_half<H16>(const void*, void*, int, long long, cudaStream_t);
+template void launch_from_half<B16>(const void*, void*, int, long long, cudaStream_t);
+template void launch_pack_gauge_half<H16>(const void*, int, void*, int, cudaStream_t);
+template void launch_pack_gauge_half<B16>(const void*, int, void*, int, cudaStream_t);
 
 template <typename R>
 void dot_rhs(const void* a, const void* b, long long n, int nrhs, double2* host_out, double2* d_partial,

@@ -20,12 +20,15 @@
 // Storage (see ovl_internal.h): FP64 spinors are 12 planes of double2 and links
 // 9 planes of double2 per direction; FP32 spinors are 6 planes of float4 (two
 // components per 16-byte load) and links keep their first two rows in 3 planes
-// of float4, the third row being rebuilt as conj(row0 x row1) (SU(3)).
+// of float4, the third row being rebuilt as conj(row0 x row1) (SU(3)).  The
+// 16-bit formats (half_store.h) are read into FP32 and computed in FP32.
 //
 // One thread per (site, rhs); each reads the 8 neighbour spinors, 8 links and
 // its own site for the mass term and the epilogue vectors.  Threads of the same
 // site and different right-hand sides sit in the same block, so the links they
 // share are read from DRAM/L2 once and from L1 after.
+#include <type_traits>
+
 #include "ovl_internal.h"
 
 namespace ovl {
@@ -86,6 +89,13 @@ template <> struct GBlock<1> { static constexpr bool diag = false; static conste
 template <> struct GBlock<2> { static constexpr bool diag = true; static constexpr int A = 3, B = 1; };   // -i s3
 template <> struct GBlock<3> { static constexpr bool diag = true; static constexpr int A = 0, B = 0; };   // 1
 
+// Row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1).
+__device__ __forceinline__ void third_row(Cx<float> (&u)[3][3]) {
+    u[2][0] = cconj(csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1])));
+    u[2][1] = cconj(csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2])));
+    u[2][2] = cconj(csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0])));
+}
+
 // ---- storage policies ------------------------------------------------------
 
 template <typename R> struct IO;
@@ -124,6 +134,7 @@ template <> struct IO<double> {
                 u[i][j] = {v.x, v.y};
             }
     }
+    static __host__ __device__ __forceinline__ long long rhs_bytes(long long V) { return 192 * V; }
 };
 
 template <> struct IO<float> {
@@ -162,11 +173,46 @@ template <> struct IO<float> {
         u[1][0] = {a1.z, a1.w};
         u[1][1] = {a2.x, a2.y};
         u[1][2] = {a2.z, a2.w};
-        u[2][0] = cconj(csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1])));
-        u[2][1] = cconj(csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2])));
-        u[2][2] = cconj(csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0])));
+        third_row(u);
     }
+    static __host__ __device__ __forceinline__ long long rhs_bytes(long long V) { return 96 * V; }
 };
+
+// 16-bit storage: converted to FP32 on load, rounded on store (half_store.h).
+template <typename S>
+struct IOHalf {
+    static __device__ __forceinline__ void load(const void* base, long long V, int s, Cx<float> (&p)[12]) {
+        float2 q[12];
+        half_load_site<S, true>(base, V, s, q);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k] = {q[k].x, q[k].y};
+    }
+    static __device__ __forceinline__ void load_plain(const void* base, long long V, int s, Cx<float> (&p)[12]) {
+        float2 q[12];
+        half_load_site<S, false>(base, V, s, q);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k] = {q[k].x, q[k].y};
+    }
+    static __device__ __forceinline__ void store(void* base, long long V, int s, const Cx<float> (&p)[12]) {
+        float2 q[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = make_float2(p[k].re, p[k].im);
+        half_store_site<S>(base, V, s, q);
+    }
+    static __device__ __forceinline__ void link(const void* U, long long V, int mu, int site, Cx<float> (&u)[3][3]) {
+        float2 r[6];
+        half_load_link<S>(U, V, mu, site, r);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            u[0][j] = {r[j].x, r[j].y};
+            u[1][j] = {r[3 + j].x, r[3 + j].y};
+        }
+        third_row(u);
+    }
+    static __host__ __device__ __forceinline__ long long rhs_bytes(long long V) { return half_rhs_bytes<S>(V); }
+};
+template <> struct IO<H16> : IOHalf<H16> {};
+template <> struct IO<B16> : IOHalf<B16> {};
 
 template <typename R>
 struct Args {
@@ -195,14 +241,14 @@ enum { kNoFac = 0, kRealFac = 1, kCplxFac = 2 };
 
 // Accumulate one hop in direction MU: forward (FWD) uses U_mu(n) psi(n+mu) with
 // (1 - gamma_mu); backward uses U_mu(n-mu)^+ psi(n-mu) with (1 + gamma_mu).
-template <typename R, int MU, bool FWD, int KIND>
+template <typename ST, int MU, bool FWD, int KIND, typename R = typename Arith<ST>::type>
 __device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, int link_site, Cx<R> fac,
                                     Cx<R> (&acc)[12]) {
     constexpr int S = FWD ? 2 : 0;  // forward: h = psi_up - G psi_dn (multiply G by -1)
     using G = GBlock<MU>;
     const long long V = a.V;
     Cx<R> p[12];
-    IO<R>::load(in, V, nb, p);
+    IO<ST>::load(in, V, nb, p);
     Cx<R> h[2][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -215,7 +261,7 @@ __device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, in
         }
     }
     Cx<R> u[3][3];
-    IO<R>::link(a.U, V, MU, link_site, u);
+    IO<ST>::link(a.U, V, MU, link_site, u);
     Cx<R> w[2][3];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -253,7 +299,7 @@ __device__ __forceinline__ void hop(const Args<R>& a, const void* in, int nb, in
 // Both hops of direction MU.  XCPLX: the x hops carry the complex factor ph (forward) and
 // conj(ph) (backward).  FP64 links carry the boundary signs (folded in when they are packed),
 // so FP64 hops are scaled only by a phase; Dirichlet hops are skipped in both precisions.
-template <typename R, int MU, bool XCPLX>
+template <typename ST, int MU, bool XCPLX, typename R = typename Arith<ST>::type>
 __device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int s, int xmu, Cx<R> ph,
                                           Cx<R> (&acc)[12]) {
     constexpr bool FOLD = sizeof(R) == sizeof(double);
@@ -265,9 +311,9 @@ __device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int 
         const R f = edge ? a.bcf[MU] : R(1);
         if (f != R(0)) {
             if constexpr (MU == 0 && XCPLX)
-                hop<R, MU, true, kCplxFac>(a, in, nb, s, FOLD ? ph : Cx<R>{f * ph.re, f * ph.im}, acc);
-            else if constexpr (FOLD) hop<R, MU, true, kNoFac>(a, in, nb, s, {f, R(0)}, acc);
-            else hop<R, MU, true, kRealFac>(a, in, nb, s, {f, R(0)}, acc);
+                hop<ST, MU, true, kCplxFac>(a, in, nb, s, FOLD ? ph : Cx<R>{f * ph.re, f * ph.im}, acc);
+            else if constexpr (FOLD) hop<ST, MU, true, kNoFac>(a, in, nb, s, {f, R(0)}, acc);
+            else hop<ST, MU, true, kRealFac>(a, in, nb, s, {f, R(0)}, acc);
         }
     }
     // backward neighbour
@@ -277,10 +323,10 @@ __device__ __forceinline__ void both_hops(const Args<R>& a, const void* in, int 
         const R f = edge ? a.bcf[MU] : R(1);
         if (f != R(0)) {
             if constexpr (MU == 0 && XCPLX)
-                hop<R, MU, false, kCplxFac>(a, in, nb, nb, FOLD ? Cx<R>{ph.re, -ph.im} : Cx<R>{f * ph.re, -f * ph.im},
-                                            acc);
-            else if constexpr (FOLD) hop<R, MU, false, kNoFac>(a, in, nb, nb, {f, R(0)}, acc);
-            else hop<R, MU, false, kRealFac>(a, in, nb, nb, {f, R(0)}, acc);
+                hop<ST, MU, false, kCplxFac>(a, in, nb, nb, FOLD ? Cx<R>{ph.re, -ph.im} : Cx<R>{f * ph.re, -f * ph.im},
+                                             acc);
+            else if constexpr (FOLD) hop<ST, MU, false, kNoFac>(a, in, nb, nb, {f, R(0)}, acc);
+            else hop<ST, MU, false, kRealFac>(a, in, nb, nb, {f, R(0)}, acc);
         }
     }
 }
@@ -317,18 +363,21 @@ template <> struct MinBlocks<double> {
     static constexpr int value = OVL_DSLASH_MIN_BLOCKS_F64;
     static constexpr int dense = OVL_DSLASH_MIN_BLOCKS_F64;
 };
+template <> struct MinBlocks<H16> : MinBlocks<float> {};
+template <> struct MinBlocks<B16> : MinBlocks<float> {};
 
 // DERIV: instead of H_w, its derivative with respect to the field phase phi of the
 // right-hand side: only the x hops depend on phi, through exp(i phi t) U_x(n) (forward)
 // and exp(-i phi t) U_x(n-x)^+ (backward), whose derivatives bring the factors i t and
 // -i t; the mass term drops out.
-template <typename R, bool DERIV, int MINB>
-__global__ void __launch_bounds__(DSLASH_THREADS, MINB) dslash_kernel(Args<R> a, int nrhs) {
+template <typename ST, bool DERIV, int MINB>
+__global__ void __launch_bounds__(DSLASH_THREADS, MINB) dslash_kernel(Args<typename Arith<ST>::type> a, int nrhs) {
+    using R = typename Arith<ST>::type;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     if (s >= a.V || r >= nrhs) return;
     const long long V = a.V;
-    const long long off = (long long)r * 12 * V * (long long)sizeof(Cx<R>);  // bytes per right-hand side
+    const long long off = (long long)r * IO<ST>::rhs_bytes(V);  // bytes per right-hand side
     const char* in = (const char*)a.in + off;
 
     int t = s;
@@ -364,16 +413,16 @@ __global__ void __launch_bounds__(DSLASH_THREADS, MINB) dslash_kernel(Args<R> a,
     const R cd = cop * a.diag, ch = R(-0.5) * cop;
     if constexpr (DERIV) {
         const R tt = (R)x3;
-        both_hops<R, 0, true>(a, in, s, x0, {-tt * ph.im, tt * ph.re}, acc);  // i t exp(i phi t)
+        both_hops<ST, 0, true>(a, in, s, x0, {-tt * ph.im, tt * ph.re}, acc);  // i t exp(i phi t)
 #pragma unroll
         for (int k = 0; k < 12; ++k) z[k] = cscale(k < 6 ? ch : -ch, acc[k]);
     } else {
-        if (a.phase) both_hops<R, 0, true>(a, in, s, x0, ph, acc);
-        else both_hops<R, 0, false>(a, in, s, x0, ph, acc);
-        both_hops<R, 1, false>(a, in, s, x1, ph, acc);
-        both_hops<R, 2, false>(a, in, s, x2, ph, acc);
-        both_hops<R, 3, false>(a, in, s, x3, ph, acc);
-        IO<R>::load(in, V, s, tmp);
+        if (a.phase) both_hops<ST, 0, true>(a, in, s, x0, ph, acc);
+        else both_hops<ST, 0, false>(a, in, s, x0, ph, acc);
+        both_hops<ST, 1, false>(a, in, s, x1, ph, acc);
+        both_hops<ST, 2, false>(a, in, s, x2, ph, acc);
+        both_hops<ST, 3, false>(a, in, s, x3, ph, acc);
+        IO<ST>::load(in, V, s, tmp);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const R sd = k < 6 ? cd : -cd, sh = k < 6 ? ch : -ch;
@@ -382,7 +431,7 @@ __global__ void __launch_bounds__(DSLASH_THREADS, MINB) dslash_kernel(Args<R> a,
     }
     // + c1 v1
     if (a.v1) {
-        IO<R>::load((const char*)a.v1 + off, V, s, tmp);
+        IO<ST>::load((const char*)a.v1 + off, V, s, tmp);
 #pragma unroll
         for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(c1, tmp[k]));
     }
@@ -403,24 +452,25 @@ __global__ void __launch_bounds__(DSLASH_THREADS, MINB) dslash_kernel(Args<R> a,
         }
     }
     if (a.v2) {
-        IO<R>::load((const char*)a.v2 + off, V, s, tmp);
+        IO<ST>::load((const char*)a.v2 + off, V, s, tmp);
 #pragma unroll
         for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(c2, tmp[k]));
     }
     if (a.v3) {
         // v3 may alias out: plain loads; the same thread reads then writes site s
-        IO<R>::load_plain((const char*)a.v3 + off, V, s, tmp);
+        IO<ST>::load_plain((const char*)a.v3 + off, V, s, tmp);
 #pragma unroll
         for (int k = 0; k < 12; ++k) z[k] = cadd(z[k], cscale(a.c3, tmp[k]));
     }
-    IO<R>::store((char*)a.out + off, V, s, z);
+    IO<ST>::store((char*)a.out + off, V, s, z);
 }
 
 }  // namespace
 
-template <typename R>
+template <typename S>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
                    const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv, int shape) {
+    using R = typename Arith<S>::type;
     Args<R> a;
     a.U = links;
     a.in = in;
@@ -452,14 +502,17 @@ void launch_dslash(const Geom& g, double m0, const void* links, const void* in, 
     const int bx = DSLASH_THREADS / by;
     dim3 block(bx, by);
     dim3 grid((g.V + bx - 1) / bx, (nrhs + by - 1) / by);
-    constexpr int mb = MinBlocks<R>::value, md = MinBlocks<R>::dense;
-    if (deriv) {
-        if (dense) dslash_kernel<R, true, md><<<grid, block, 0, s>>>(a, nrhs);
-        else dslash_kernel<R, true, mb><<<grid, block, 0, s>>>(a, nrhs);
-    } else {
-        if (dense) dslash_kernel<R, false, md><<<grid, block, 0, s>>>(a, nrhs);
-        else dslash_kernel<R, false, mb><<<grid, block, 0, s>>>(a, nrhs);
+    constexpr int mb = MinBlocks<S>::value, md = MinBlocks<S>::dense;
+    if constexpr (std::is_same<S, R>::value) {  // the field derivative: FP64 and FP32 storage only
+        if (deriv) {
+            if (dense) dslash_kernel<S, true, md><<<grid, block, 0, s>>>(a, nrhs);
+            else dslash_kernel<S, true, mb><<<grid, block, 0, s>>>(a, nrhs);
+            count_launch();
+            return;
+        }
     }
+    if (dense) dslash_kernel<S, false, md><<<grid, block, 0, s>>>(a, nrhs);
+    else dslash_kernel<S, false, mb><<<grid, block, 0, s>>>(a, nrhs);
     count_launch();
 }
 
@@ -467,5 +520,9 @@ template void launch_dslash<double>(const Geom&, double, const void*, const void
                                     const Epilogue&, cudaStream_t, bool, int);
 template void launch_dslash<float>(const Geom&, double, const void*, const void*, void*, int, const double*,
                                    const Epilogue&, cudaStream_t, bool, int);
+template void launch_dslash<H16>(const Geom&, double, const void*, const void*, void*, int, const double*,
+                                 const Epilogue&, cudaStream_t, bool, int);
+template void launch_dslash<B16>(const Geom&, double, const void*, const void*, void*, int, const double*,
+                                 const Epilogue&, cudaStream_t, bool, int);
 
 }  // namespace ovl

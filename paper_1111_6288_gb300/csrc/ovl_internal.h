@@ -6,12 +6,16 @@
 //   FP32 spinor  [rhs][6][V]  float4 = components (2q, 2q+1); spins 0,1 are planes 0-2
 //   FP64 links   [4][9][V]    double2, entry 3*a + b of U_mu(n)
 //   FP32 links   [4][3][V]    float4 = rows 0 and 1 of U_mu(n); row 2 = conj(row0 x row1)
+//   FP16 / BF16  spinors [rhs][3][V] uint4 (+ a float scale per site for FP16) and links
+//                rows 0 and 1 in 24 bytes, FP32 arithmetic (half_store.h)
 //   bank         [n_ev][...]  the spinor layout of its precision
 // A spinor vector is 12 V complex numbers (192 B or 96 B per site) in both precisions,
 // so element-wise kernels and inner products treat vectors as flat complex arrays.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "half_store.h"
 
 #include <atomic>
 #include <cstdint>
@@ -27,6 +31,11 @@ inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_
 template <typename R> struct C2;
 template <> struct C2<double> { typedef double2 T; };
 template <> struct C2<float> { typedef float2 T; };
+
+// Arithmetic type of a storage type: itself for FP64 and FP32, FP32 for the 16-bit formats.
+template <typename S> struct Arith { typedef S type; };
+template <> struct Arith<H16> { typedef float type; };
+template <> struct Arith<B16> { typedef float type; };
 
 // Lattice geometry and boundary factors (1 periodic, -1 antiperiodic, 0 Dirichlet).
 struct Geom {
@@ -54,6 +63,7 @@ struct Epilogue {
 };
 
 // ---- kernels: dslash.cu ---------------------------------------------------
+// S: storage type (double, float, H16, B16; the 16-bit ones compute in FP32).
 // deriv: apply dH_w/dphi (the phi-derivative of the x hops, per right-hand-side phase) in
 // place of H_w; the epilogue is the same.  shape: right-hand sides per thread block in the
 // low bits (1, 2 or 4; 0 = default), | kShapeDense for the FP32 kernel whose registers allow
@@ -78,6 +88,14 @@ void launch_pack_gauge(const void* abi, int dtype_in, void* internal, const Geom
 // Conversion of nvec spinor vectors between precisions (and internal layouts).
 template <typename RI, typename RO>
 void launch_convert(const void* in, void* out, int V, long long nvec, cudaStream_t s);
+// FP32 spinors -> 16-bit storage S (times factor, then rounded), and back.
+template <typename S>
+void launch_to_half(const void* in32, void* out, int V, long long nvec, double factor, cudaStream_t s);
+template <typename S>
+void launch_from_half(const void* in, void* out32, int V, long long nvec, cudaStream_t s);
+// ABI links -> 16-bit storage S (rows 0 and 1).
+template <typename S>
+void launch_pack_gauge_half(const void* abi, int dtype_in, void* internal, int V, cudaStream_t s);
 
 // Per-rhs reductions over n complex numbers each (vectors at stride n).  Results are
 // written to host memory after an internal synchronisation of s.  Deterministic.
