@@ -99,6 +99,11 @@ typedef struct ov_params {
     int max_iter;         /* cap on inner CG iterations per solve (<= 0: 100000) */
     double inner_tol;     /* relative tolerance of each inner solve (<= 0: default,
                              1e-6 for F32; for F64 the outer target itself) */
+    int launch_shape;     /* Wilson-kernel launch shape of the polynomial loops: 0 = timed per
+                             batch size (ov_tune_info); else 1, 2 or 4 systems per thread block,
+                             | 8 for the FP32 register budget of 7 blocks per SM instead of 6,
+                             | 16 for the kernel that stages x-rows in shared memory (used where
+                             the lattice allows it, see ov_tune_info). */
 } ov_params;
 
 /* Per-solve statistics, filled on the host when solve_overlap returns. */
@@ -136,8 +141,14 @@ const char* ov_last_error(const ov_ctx* ctx);
 const char* ov_last_info(const ov_ctx* ctx);
 /* Timings of the Wilson-kernel launch shapes the library tried for each batch size it met
  * (1, 2 or 4 systems per thread block; "d": FP32 registers capped for 7 resident blocks per SM
- * instead of 6); the fastest is used from then on. */
+ * instead of 6; "t": the kernel that stages whole x-rows in shared memory with bulk copies,
+ * offered when Lx is a multiple of 4 and rows of Lx sites tile a 32-multiple block); the
+ * fastest is used from then on. */
 const char* ov_tune_info(const ov_ctx* ctx);
+/* Synchronise stream; OV_ERR_TIMEOUT if a bounded wait inside a kernel ran out since the
+ * last check (its output is then incomplete), OV_ERR_CUDA if the stream reports an error.
+ * solve_overlap and ov_eigensolve_Q make the same check before they return. */
+int ov_sync(ov_ctx* ctx, ov_stream_t stream);
 /* Number of lattice sites. */
 long long ov_volume(const ov_ctx* ctx);
 /* ||H_w|| in use (after the hw_norm <= 0 default is resolved). */

@@ -41,5 +41,6 @@ from ._ovl import (  # noqa: F401
     library_path,
     pion_correlator,
     solve_overlap,
+    sync,
     timeslice_scale,
 )

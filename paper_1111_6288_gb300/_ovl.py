@@ -39,6 +39,7 @@ class _Params(C.Structure):
         ("max_nrhs", C.c_int),
         ("max_iter", C.c_int),
         ("inner_tol", C.c_double),
+        ("launch_shape", C.c_int),
     ]
 
 
@@ -72,6 +73,7 @@ _SIGNATURES = {
     "ov_last_error": (C.c_char_p, [_VP]),
     "ov_last_info": (C.c_char_p, [_VP]),
     "ov_tune_info": (C.c_char_p, [_VP]),
+    "ov_sync": (_I, [_VP, _VP]),
     "ov_volume": (C.c_longlong, [_VP]),
     "ov_hw_norm": (_D, [_VP]),
     "ov_poly_delta": (_D, [_VP]),
@@ -154,6 +156,7 @@ class Params:
     max_nrhs: int = 12
     max_iter: int = 0
     inner_tol: float = 0.0
+    launch_shape: int = 0
 
 
 @dataclass
@@ -185,6 +188,7 @@ class Context:
         p.max_nrhs = params.max_nrhs
         p.max_iter = params.max_iter
         p.inner_tol = params.inner_tol
+        p.launch_shape = params.launch_shape
         h = C.c_void_p()
         rc = lib().ov_create(C.byref(p), C.byref(h))
         _check(rc, None)
@@ -295,6 +299,11 @@ def apply_wilson(ctx: Context, x, out, phase=None, hermitian=False, stream=None)
                             _stream(stream))
     _check(rc, ctx.handle)
     return out
+
+
+def sync(ctx: Context, stream=None):
+    """Synchronise the stream; raises OvlError (OV_ERR_TIMEOUT) if a bounded device wait ran out."""
+    _check(lib().ov_sync(ctx.handle, _stream(stream)), ctx.handle)
 
 
 def apply_sign_Hw(ctx: Context, x, out, phase=None, stream=None):

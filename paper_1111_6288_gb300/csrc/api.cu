@@ -276,12 +276,14 @@ bool any_phase(const SysSet& S) {
     return false;
 }
 
-// Launch shape of the Wilson kernel for ns systems of storage type R (right-hand sides per block,
-// and for FP32 arithmetic the 6- or 7-blocks-per-SM register budget): timed once on the sign
-// pipeline's own buffers (the Clenshaw-step launch with its epilogue), fastest kept.
+// Launch shape of the Wilson kernel for ns systems of storage type R (right-hand sides per block;
+// for FP32 arithmetic also the 6- or 7-blocks-per-SM register budget and, where the lattice
+// allows, the tiled kernel): timed once on the sign pipeline's own buffers (the Clenshaw-step
+// launch with its epilogue), fastest kept.
 template <typename R>
 int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* in, void* v1, void* v2,
                 void* v3, void* out, cudaStream_t s) {
+    if (c->p.launch_shape > 0) return c->p.launch_shape;  // fixed by the caller
     const auto key = std::make_pair(prec_of<R>(), ns);
     auto it = c->launch_shape.find(key);
     if (it != c->launch_shape.end()) return it->second;
@@ -289,7 +291,13 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
     for (int by : {1, 2, 4}) {
         if (by > ns) break;
         shapes.push_back(by);
-        if (!std::is_same<R, double>::value) shapes.push_back(by | kShapeDense);
+        if (!std::is_same<R, double>::value) {
+            shapes.push_back(by | kShapeDense);
+            if (tile_rows(c->g, by) > 0) {
+                shapes.push_back(by | kShapeTiled);
+                shapes.push_back(by | kShapeTiled | kShapeDense);
+            }
+        }
     }
     int best = shapes[0];
     if (shapes.size() > 1) {
@@ -314,8 +322,8 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            snprintf(buf, sizeof(buf), "%s%d%s:%.1fus", sh == shapes[0] ? "" : " ", sh & kShapeRhsMask,
-                     (sh & kShapeDense) ? "d" : "", 1e3f * ms / 5);
+            snprintf(buf, sizeof(buf), "%s%d%s%s:%.1fus", sh == shapes[0] ? "" : " ", sh & kShapeRhsMask,
+                     (sh & kShapeDense) ? "d" : "", (sh & kShapeTiled) ? "t" : "", 1e3f * ms / 5);
             c->tune_log += buf;
             if (ms < best_ms) {
                 best_ms = ms;
@@ -551,14 +559,15 @@ int apply_generic(ov_ctx* c, const void* in, void* out, int nrhs, const double* 
         Epilogue e;
         e.g5 = (kind == 0);  // gamma5 H_w = D_w
         const double* d_phase = any_phase(S) ? c->d_phase : nullptr;
+        const int shape = c->p.launch_shape;  // 0: the default shape
         if constexpr (std::is_same<R, ST>::value) {
-            launch_dslash<R>(c->g, c->p.m0, links_of<R>(c), X, Y, nrhs, d_phase, e, s);
+            launch_dslash<R>(c->g, c->p.m0, links_of<R>(c), X, Y, nrhs, d_phase, e, s, false, shape);
         } else {  // input rounded to the 16-bit format, output read back into FP32
             void *Xh, *Yh;
             TRY(workspace(c, "io_in", prec_of<ST>(), nrhs, &Xh));
             TRY(workspace(c, "io_out", prec_of<ST>(), nrhs, &Yh));
             launch_to_half<ST>(X, Xh, c->g.V, nrhs, 1.0, s);
-            launch_dslash<ST>(c->g, c->p.m0, links_of<ST>(c), Xh, Yh, nrhs, d_phase, e, s);
+            launch_dslash<ST>(c->g, c->p.m0, links_of<ST>(c), Xh, Yh, nrhs, d_phase, e, s, false, shape);
             launch_from_half<ST>(Yh, Y, c->g.V, nrhs, s);
         }
         CKL();
@@ -826,6 +835,12 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     if (p->max_nrhs < 1 || p->max_nrhs > kMaxRhs / 2)
         return fail(c, OV_ERR_ARG, "max_nrhs = %d outside [1, %d]", p->max_nrhs, kMaxRhs / 2);
     if (!std::isfinite(p->m0)) return fail(c, OV_ERR_ARG, "m0 not finite");
+    {
+        const int rb = p->launch_shape & kShapeRhsMask;
+        if (p->launch_shape < 0 || (p->launch_shape & ~(kShapeRhsMask | kShapeDense | kShapeTiled)) ||
+            (p->launch_shape > 0 && rb != 1 && rb != 2 && rb != 4))
+            return fail(c, OV_ERR_ARG, "launch_shape = %d invalid", p->launch_shape);
+    }
     c = new ov_ctx();
     c->p = *p;
     for (int mu = 0; mu < 4; ++mu) {
@@ -891,6 +906,15 @@ const char* ov_last_error(const ov_ctx* c) { return c ? c->err.c_str() : g_creat
 const char* ov_last_info(const ov_ctx* c) { return c ? c->info.c_str() : ""; }
 
 const char* ov_tune_info(const ov_ctx* c) { return c ? c->tune_log.c_str() : ""; }
+
+int ov_sync(ov_ctx* c, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    const int t = take_wait_timeouts();
+    if (t < 0) return fail(c, OV_ERR_CUDA, "reading the device wait flag failed");
+    if (t > 0) return fail(c, OV_ERR_TIMEOUT, "a bounded device wait ran out");
+    return OV_OK;
+}
 
 long long ov_volume(const ov_ctx* c) { return c ? c->g.V : 0; }
 
@@ -1116,6 +1140,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     }
     if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
     CK(cudaStreamSynchronize(s));
+    if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "eigensolver: a bounded device wait ran out");
     {
         char buf[256];
         snprintf(buf, sizeof(buf),
@@ -1384,6 +1409,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
     launch_unpack_spinor<double>(X, x, OV_C128, V, nrhs, s);
     CKL();
     CK(cudaStreamSynchronize(s));
+    if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "solve_overlap: a bounded device wait ran out");
     c->info = hist;
     if (st) {
         st->status = status;

@@ -68,8 +68,15 @@ struct Epilogue {
 // place of H_w; the epilogue is the same.  shape: right-hand sides per thread block in the
 // low bits (1, 2 or 4; 0 = default), | kShapeDense for the FP32 kernel whose registers allow
 // 7 resident blocks per SM instead of 6 (no effect in FP64).
+// | kShapeTiled: the FP32 / 16-bit kernel that stages whole x-rows in shared memory (lattices
+// for which tile_rows() > 0; otherwise the plain kernel runs).
 constexpr int kShapeRhsMask = 7;
 constexpr int kShapeDense = 8;
+constexpr int kShapeTiled = 16;
+// Rows of x per block of the tiled kernel for `by` right-hand sides per block (0: not tileable).
+int tile_rows(const Geom& g, int by);
+// 1 if a bounded device wait ran out since the last call (and clears it), 0 if not, -1 on error.
+int take_wait_timeouts();
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
                    const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv = false,
