@@ -11,9 +11,11 @@ eq. 2), the 50 lowest |lambda| eigenvectors of Q treated exactly, quark mass
 
 A step is one solve (every row of the hot path: Wilson kernels, Clenshaw
 polynomial, small-space projection, sign, D(m), chiral-sector CG in FP32
-with FP64 true-residual correction).  ``value`` counts D_ov applications
-(sign(H_w) applied to one right-hand side, any precision) per second
-sustained inside the timed solves.  Also reported: the FP64-only solve
+with FP64 true-residual correction; by default the inner cycles run at the
+adaptive order's lower degrees, every true residual at the full degree).
+``value`` counts D_ov applications at the full degree per second sustained
+inside the timed solves: Wilson applications of the solves (any precision)
+divided by 2n + 1.  Also reported: the FP64-only solve
 (time-to-solution against the mixed one), isolated FP32/FP64 D(m)
 applications, the Wilson-kernel bandwidth of the Clenshaw loops (roofline),
 and the CPU oracle's rate on a bounded sample.
@@ -51,7 +53,7 @@ WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV
 # ncu: DRAM bytes of the FP32 Wilson kernel over its algorithmic bytes on the bench lattice with warm
 # caches (plain and Clenshaw-epilogue launches, profiles/dslash_f32_16x16x16x32_warm_l2.md): the
 # loop's vectors and links stay in L2.  Set to None whenever the kernel changes until re-measured.
-DRAM_OVER_ALGORITHMIC = 0.32
+DRAM_OVER_ALGORITHMIC = None
 
 
 def dist_env():
@@ -215,11 +217,12 @@ def run_reference(args):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_case(dims, precision="f32"):
+def kernel_case(dims, precision="f32", shape=0):
     """A few Wilson-kernel launches (plain and Clenshaw-epilogue) on one lattice.
 
-    FP32: the first 12 launches time the two launch shapes, then the Clenshaw steps follow
-    (plain, epilogue, ...).  FP64 has one shape and no timing launches."""
+    The first D(m) application times the launch shapes and captures the loop's graph; the
+    second, inside the NVTX range "kernel_case", runs the Clenshaw steps (plain, epilogue,
+    ...) with the shape the library picked."""
     import torch
 
     import paper_1111_6288_gb300 as P
@@ -228,14 +231,18 @@ def kernel_case(dims, precision="f32"):
     prec = P.OV_PREC_F32 if precision == "f32" else P.OV_PREC_F64
     U = torch.from_numpy(synth.random_su3_field(dims, LINK_EPS, 0)).cuda()
     ctx = P.Context(P.Params(dims=dims, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=4, precision=prec,
-                             inner_precision=prec, max_nrhs=1))
+                             inner_precision=prec, max_nrhs=1, launch_shape=shape))
     ctx.set_gauge(U)
     del U
     x = torch.from_numpy(synth.gaussian_spinor(dims, 1, 1)).to(ctx.spinor_dtype()).cuda()
     y = torch.empty_like(x)
-    for _ in range(2):
-        P.apply_overlap(ctx, x, y, mass=MASS)
+    P.apply_overlap(ctx, x, y, mass=MASS)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("kernel_case")
+    P.apply_overlap(ctx, x, y, mass=MASS)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print("launch shapes timed:", ctx.tune_info)
     ctx.close()
 
 
@@ -246,12 +253,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the FP64-only comparison solve")
+    ap.add_argument("--fixed-order", action="store_true",
+                    help="inner solves at the full polynomial degree (default: adaptive order per outer cycle)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling case: a few FP32 Wilson-kernel launches (default 24^3x48), "
                          "then exit without a JSON line")
     ap.add_argument("--kernel-dims", default="24,24,24,48", help="lattice of the profiling case: Lx,Ly,Lz,Lt")
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"], help="precision of the profiling case")
+    ap.add_argument("--kernel-shape", type=int, default=0,
+                    help="launch shape of the profiling case (ov_params.launch_shape; 0 = timed by the library)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -260,7 +271,7 @@ def main():
         run_reference(args)
         return
     if args.kernel_case:
-        kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision)
+        kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision, args.kernel_shape)
         return
 
     import numpy as np
@@ -285,7 +296,8 @@ def main():
     stream = torch.cuda.current_stream()
     U = torch.from_numpy(synth.random_su3_field(DIMS, LINK_EPS, 0)).to(dev)
     common = dict(dims=DIMS, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE, max_nrhs=2)
-    ctx_mix = P.Context(P.Params(precision=P.OV_PREC_F32, inner_precision=P.OV_PREC_F32, **common))
+    ctx_mix = P.Context(P.Params(precision=P.OV_PREC_F32, inner_precision=P.OV_PREC_F32,
+                                 adaptive_order=0 if args.fixed_order else 1, **common))
     ctx_64 = P.Context(P.Params(precision=P.OV_PREC_F64, inner_precision=P.OV_PREC_F64, **common))
     ctx_mix.set_gauge(U)
     ctx_64.set_gauge(U)
@@ -339,7 +351,10 @@ def main():
     prof32 = ctx_mix.read_profile(P.OV_PREC_F32)
     prof64 = ctx_mix.read_profile(P.OV_PREC_F64)
     local_ms = ev0.elapsed_time(ev1)
-    applies = float(sum(s.sign_applies for s in stats))
+    # D_ov applications at the full degree n: Wilson applications / (2n + 1), so that the lower
+    # degrees of the adaptive order's inner cycles count for the work they do
+    per_apply = 2 * DEGREE + 1
+    applies = float(sum(s.dslash_calls for s in stats)) / per_apply
     max_ms, total_applies = aggregate(local_ms, applies, world)
     value = total_applies / (max_ms / 1e3)
     worst_res = max(s.true_residual for s in stats)
@@ -358,7 +373,7 @@ def main():
         x.zero_()
         st = P.solve_overlap(ctx_mix, b, x, MASS, tol=TOL)
         x_host.copy_(x, non_blocking=True)
-        e2e_applies += st.sign_applies
+        e2e_applies += st.dslash_calls / per_apply
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms, e2e_total = aggregate(e0.elapsed_time(e1), e2e_applies, world)
@@ -441,11 +456,17 @@ def main():
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "links": f"exp(i {LINK_EPS} H), seed 0",
                        "m0": M0, "poly_degree": DEGREE, "sqrt_eps": SQRT_EPS, "n_ev": N_EV, "mass": MASS,
                        "tol": TOL, "precision": "FP32 inner CG and Clenshaw, FP64 true residual and update",
+                       "polynomial": (f"n = {DEGREE} everywhere" if args.fixed_order else
+                                      f"n = {DEGREE} in every true residual; each inner cycle at the lowest degree "
+                                      "with delta <= 0.5 m g (adaptive order)"),
+                       "value_unit": f"D_ov applications at n = {DEGREE}: Wilson applications / {2 * DEGREE + 1}",
                        "parallelism": f"replicas x{world}", "l2": "256 MB flush before every step"},
             "time_to_solution": {"mixed_s": mean_mixed_s, "fp64_s": fp64["seconds"] if fp64 else None,
                                  "speedup": (fp64["seconds"] / mean_mixed_s) if fp64 else None,
                                  "mixed_outer_iters": stats[0].outer_iters, "mixed_inner_iters": stats[0].inner_iters,
                                  "mixed_sign_applies": stats[0].sign_applies,
+                                 "mixed_wilson_applies": stats[0].dslash_calls,
+                                 "mixed_cycles": ctx_mix.last_info,
                                  "mixed_true_residual": worst_res, "fp64": fp64},
             "dov_apply_per_s": {"f32": rate32, "f64": rate64, **rates_half},
             "dov_error_vs_f64": errors,

@@ -104,6 +104,10 @@ typedef struct ov_params {
                              | 8 for the FP32 register budget of 7 blocks per SM instead of 6,
                              | 16 for the kernel that stages x-rows in shared memory (used where
                              the lattice allows it, see ov_tune_info). */
+    int adaptive_order;   /* solve_overlap: 0 = every inner sign application at poly_degree;
+                             1 = per outer cycle, the lowest degree (a multiple of 8) whose
+                             interpolant has delta <= 0.5 m g, g = the cycle's inner tolerance
+                             (the true residual keeps poly_degree; needs coeffs = NULL) */
 } ov_params;
 
 /* Per-solve statistics, filled on the host when solve_overlap returns. */
@@ -155,6 +159,12 @@ long long ov_volume(const ov_ctx* ctx);
 double ov_hw_norm(const ov_ctx* ctx);
 /* delta = max over [eps, 1] of |1 - sqrt(x) P(x)| for the polynomial in use (Sec. 2, eq. 2). */
 double ov_poly_delta(const ov_ctx* ctx);
+/* delta of the degree-n Chebyshev interpolant of x^{-1/2} on [eps, 1] (as ov_poly_delta, no
+ * context needed); -1 for invalid arguments. */
+double ov_poly_delta_n(int n, double eps);
+/* The degree the adaptive order picks for a polynomial error target: the lowest multiple of 8
+ * whose interpolant on the context's interval has delta <= delta_target, else poly_degree. */
+int ov_adaptive_degree(ov_ctx* ctx, double delta_target);
 
 /* Turn event timing of the polynomial loops on (on != 0) or off. */
 int ov_set_profiling(ov_ctx* ctx, int on);

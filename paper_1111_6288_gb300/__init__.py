@@ -40,6 +40,7 @@ from ._ovl import (  # noqa: F401
     lib,
     library_path,
     pion_correlator,
+    poly_delta,
     solve_overlap,
     sync,
     timeslice_scale,

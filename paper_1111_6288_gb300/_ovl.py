@@ -40,6 +40,7 @@ class _Params(C.Structure):
         ("max_iter", C.c_int),
         ("inner_tol", C.c_double),
         ("launch_shape", C.c_int),
+        ("adaptive_order", C.c_int),
     ]
 
 
@@ -77,6 +78,8 @@ _SIGNATURES = {
     "ov_volume": (C.c_longlong, [_VP]),
     "ov_hw_norm": (_D, [_VP]),
     "ov_poly_delta": (_D, [_VP]),
+    "ov_poly_delta_n": (_D, [_I, _D]),
+    "ov_adaptive_degree": (_I, [_VP, _D]),
     "ov_set_gauge": (_I, [_VP, _VP, _I, _VP]),
     "ov_set_profiling": (_I, [_VP, _I]),
     "ov_read_profile": (_I, [_VP, _I, C.POINTER(_Profile)]),
@@ -157,6 +160,7 @@ class Params:
     max_iter: int = 0
     inner_tol: float = 0.0
     launch_shape: int = 0
+    adaptive_order: int = 0
 
 
 @dataclass
@@ -189,6 +193,7 @@ class Context:
         p.max_iter = params.max_iter
         p.inner_tol = params.inner_tol
         p.launch_shape = params.launch_shape
+        p.adaptive_order = params.adaptive_order
         h = C.c_void_p()
         rc = lib().ov_create(C.byref(p), C.byref(h))
         _check(rc, None)
@@ -229,6 +234,10 @@ class Context:
     def delta(self):
         """Error |1 - sqrt(x) P(x)| of the polynomial in use, maximised over [eps, 1]."""
         return float(lib().ov_poly_delta(self.handle))
+
+    def adaptive_degree(self, delta_target):
+        """Degree the adaptive order picks for a polynomial error target (host; no GPU)."""
+        return int(lib().ov_adaptive_degree(self.handle, float(delta_target)))
 
     @property
     def site_shape(self):
@@ -387,6 +396,14 @@ def chebyshev_coeffs(n, eps):
     out = np.zeros(n + 1)
     _check(lib().ov_chebyshev_coeffs(int(n), float(eps), out.ctypes.data_as(_DP)))
     return out
+
+
+def poly_delta(n, eps):
+    """delta = max over [eps, 1] of |1 - sqrt(x) P(x)| of the library's degree-n interpolant (host)."""
+    v = float(lib().ov_poly_delta_n(int(n), float(eps)))
+    if v < 0:
+        raise OvlError(1, "ov_poly_delta_n: invalid arguments")
+    return v
 
 
 def host_eigh(A):

@@ -57,6 +57,10 @@ struct ov_ctx {
     std::vector<double> coeffs;
     double hw_norm = 0.0;
     double delta = 0.0;  // max over [eps, 1] of |1 - sqrt(x) P(x)| (Sec. 2, eq. 2)
+    bool custom_coeffs = false;  // the caller gave the coefficients (no lower-degree interpolants)
+    // lower-degree interpolants of x^{-1/2} on the same interval and their delta, by degree
+    std::map<int, std::vector<double>> coeff_sets;
+    std::map<int, double> delta_of;
     std::string err;
     std::string info;  // summary of the last eigensolver / solve call
     void* U64 = nullptr;
@@ -216,6 +220,45 @@ Bank* find_bank(ov_ctx* c, double phase) {
     return nullptr;
 }
 
+// Coefficients of the degree-n interpolant of x^{-1/2} on the context's interval (n = poly_degree:
+// the context's own, which may be the caller's).
+const std::vector<double>& coeffs_of(ov_ctx* c, int n) {
+    if (n == c->p.poly_degree) return c->coeffs;
+    auto it = c->coeff_sets.find(n);
+    if (it == c->coeff_sets.end()) {
+        std::vector<double> cf(n + 1);
+        host_chebyshev_coeffs(n, c->p.eps, cf.data());
+        it = c->coeff_sets.emplace(n, std::move(cf)).first;
+    }
+    return it->second;
+}
+
+double delta_of_degree(ov_ctx* c, int n) {
+    if (n == c->p.poly_degree) return c->delta;
+    auto it = c->delta_of.find(n);
+    if (it != c->delta_of.end()) return it->second;
+    const std::vector<double>& cf = coeffs_of(c, n);
+    const double dl = host_poly_delta(cf.data(), n, c->p.eps);
+    c->delta_of[n] = dl;
+    return dl;
+}
+
+// Smallest degree, a multiple of 8, whose interpolant has delta <= target (delta falls with the
+// degree, eq. 2); poly_degree itself when no lower one does or when the coefficients are the
+// caller's.
+int degree_for_delta(ov_ctx* c, double target) {
+    const int N = c->p.poly_degree;
+    if (c->custom_coeffs || !(target > c->delta)) return N;
+    int lo = 1, hi = (N - 1) / 8;  // degrees 8k < N
+    if (hi < 1 || delta_of_degree(c, 8 * hi) > target) return N;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (delta_of_degree(c, 8 * mid) <= target) hi = mid;
+        else lo = mid + 1;
+    }
+    return 8 * lo;
+}
+
 // ---- small kernels local to the orchestration --------------------------------
 
 template <typename R>
@@ -343,8 +386,11 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
 // ST: storage of the links and vectors of the recurrence: R itself, or (R = float) a 16-bit
 // format, x_perp then being rounded to it and P(Q^2) x_perp read back into FP32 for the final
 // FP32 application of H_w.
+// degree: of the polynomial (0: the context's poly_degree; lower degrees use the interpolant of
+// that degree on the same interval).
 template <typename R, typename ST = R>
-int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogue fin, void* out, cudaStream_t s) {
+int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogue fin, void* out, cudaStream_t s,
+                  int degree = 0) {
     constexpr bool HALF = !std::is_same<R, ST>::value;
     const int prec = prec_of<R>();
     const int precs = prec_of<ST>();
@@ -406,7 +452,8 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     // Y = (2 Q^2 - (1 + eps))/(1 - eps) = alpha H_w^2 + beta/2:
     //   b_n = c_n x_perp;  b_k = c_k x_perp + 2 Y b_{k+1} - b_{k+2};
     //   p = c_0 x_perp + Y b_1 - b_2.
-    const int n = c->p.poly_degree;
+    const int n = degree > 0 ? degree : c->p.poly_degree;
+    const std::vector<double>& cf = coeffs_of(c, n);
     const double eps = c->p.eps, h = c->hw_norm;
     const double alpha = 4.0 / ((1.0 - eps) * h * h);
     const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
@@ -423,9 +470,9 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     auto enqueue = [&](cudaStream_t st) -> void* {
         if constexpr (HALF) {
             launch_to_half<ST>(xperp, xs, V, ns, 1.0, st);
-            launch_to_half<ST>(xperp, bA, V, ns, c->coeffs[n], st);
+            launch_to_half<ST>(xperp, bA, V, ns, cf[n], st);
         } else {
-            launch_scale<R>(c->coeffs[n], xperp, bA, (long long)ns * n12, st);
+            launch_scale<R>(cf[n], xperp, bA, (long long)ns * n12, st);
         }
         void* b1 = bA;
         void* b2 = nullptr;
@@ -437,7 +484,7 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
             e.c_op = alpha * half;
             e.c1 = beta * half;
             e.v1 = b1;
-            e.c2 = c->coeffs[k];
+            e.c2 = cf[k];
             e.v2 = xs;
             e.c3 = -1.0;
             e.v3 = b2;
@@ -462,7 +509,7 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
     void* b1 = nullptr;
     if (c->use_graphs) {
         char key[256];
-        snprintf(key, sizeof(key), "%d/%d/%d/%p/%p/%p/%p/%p/%p/%p", precs, ns, rb, xperp, xs, bA, bB, t,
+        snprintf(key, sizeof(key), "%d/%d/%d/%d/%p/%p/%p/%p/%p/%p/%p", precs, n, ns, rb, xperp, xs, bA, bB, t,
                  (const void*)d_phase, Us);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
@@ -506,14 +553,15 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
 
 // D(m) X (g5_in = false) or D(m)^+ X (g5_in = true) on internal vectors.
 template <typename R, typename ST = R>
-int overlap_op(ov_ctx* c, const void* X, const SysSet& S, double mass, bool dagger, void* out, cudaStream_t s) {
+int overlap_op(ov_ctx* c, const void* X, const SysSet& S, double mass, bool dagger, void* out, cudaStream_t s,
+               int degree = 0) {
     Epilogue fin;
     fin.c_op = (1.0 - 0.5 * mass) / c->hw_norm;
     fin.c1 = 1.0 - 0.5 * mass;
     fin.g5 = dagger ? 0 : 1;
     fin.c2 = 1.0 + 0.5 * mass;
     fin.v2 = X;
-    return sign_pipeline<R, ST>(c, X, S, dagger, fin, out, s);
+    return sign_pipeline<R, ST>(c, X, S, dagger, fin, out, s, degree);
 }
 
 int check_ready(ov_ctx* c, const void* in, const void* out, int nrhs) {
@@ -853,24 +901,8 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     else host_chebyshev_coeffs(p->poly_degree, p->eps, c->coeffs.data());
     c->p.coeffs = nullptr;
     c->hw_norm = p->hw_norm > 0.0 ? p->hw_norm : std::fabs(4.0 + p->m0) + 4.0;
-    {
-        // delta of the polynomial on a grid uniform in the Chebyshev angle (Clenshaw in FP64)
-        const int ng = 4096, n = p->poly_degree;
-        double worst = 0.0;
-        for (int q = 0; q <= ng; ++q) {
-            const double y = std::cos(3.141592653589793 * q / ng);
-            double b1 = 0.0, b2 = 0.0;
-            for (int k = n; k >= 1; --k) {
-                const double b0 = c->coeffs[k] + 2.0 * y * b1 - b2;
-                b2 = b1;
-                b1 = b0;
-            }
-            const double P = c->coeffs[0] + y * b1 - b2;
-            const double x = ((1.0 - p->eps) * y + 1.0 + p->eps) / 2.0;
-            worst = std::max(worst, std::fabs(1.0 - std::sqrt(x) * P));
-        }
-        c->delta = worst;
-    }
+    c->delta = host_poly_delta(c->coeffs.data(), p->poly_degree, p->eps);
+    c->custom_coeffs = p->coeffs != nullptr;
     if (c->p.max_iter <= 0) c->p.max_iter = 100000;
     *out = c;
     return OV_OK;
@@ -921,6 +953,18 @@ long long ov_volume(const ov_ctx* c) { return c ? c->g.V : 0; }
 double ov_hw_norm(const ov_ctx* c) { return c ? c->hw_norm : 0.0; }
 
 double ov_poly_delta(const ov_ctx* c) { return c ? c->delta : 0.0; }
+
+double ov_poly_delta_n(int n, double eps) {
+    if (n < 1 || n > 100000 || !(eps > 0.0 && eps < 1.0)) return -1.0;
+    std::vector<double> cf(n + 1);
+    host_chebyshev_coeffs(n, eps, cf.data());
+    return host_poly_delta(cf.data(), n, eps);
+}
+
+int ov_adaptive_degree(ov_ctx* c, double delta_target) {
+    if (!c) return 0;
+    return degree_for_delta(c, delta_target);
+}
 
 int ov_chebyshev_coeffs(int n, double eps, double* out) {
     if (n < 0 || !out || !(eps > 0.0 && eps < 1.0)) return OV_ERR_ARG;
@@ -1168,7 +1212,7 @@ namespace {
 // systems that still iterate; Y is put back in the original order at the end.
 template <typename R>
 int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, const std::vector<double>& tol_rel0,
-             int max_iter, int* iters, cudaStream_t s) {
+             int max_iter, int* iters, cudaStream_t s, int degree = 0) {
     const int prec = prec_of<R>();
     const int ns = S0.n;
     const long long n12 = 12LL * c->g.V;
@@ -1232,7 +1276,7 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
         A.n = na;
         A.phase.assign(S.phase.begin(), S.phase.begin() + na);
         A.chi.assign(S.chi.begin(), S.chi.begin() + na);
-        TRY(sign_pipeline<R>(c, p, A, false, fin, Ap, s));
+        TRY(sign_pipeline<R>(c, p, A, false, fin, Ap, s, degree));
         dot_rhs<R>(p, Ap, n12, na, pap.data(), c->d_partial, c->d_red, s);
         for (int k = 0; k < na; ++k) {
             if (!std::isfinite(pap[k].x) || !std::isfinite(rr[k]))
@@ -1373,8 +1417,18 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         else
             launch_convert<double, float>(S64, Bs, V, ns, s);
         CKL();
+        // Degree of this cycle's polynomial (adaptive order, Sec. 3.2): a polynomial error delta
+        // in the correction changes the corrected residual by about delta / m of the current one
+        // (|D(m)^-1| ~ 1/m), so a cycle whose smallest inner tolerance is g needs delta <= eta m g,
+        // eta = 0.5; the true residual keeps the full degree.
+        int degree = 0;
+        if (c->p.adaptive_order && ns > 0) {
+            double g = 1.0;
+            for (double t : tol_rel) g = std::min(g, t);
+            degree = degree_for_delta(c, 0.5 * std::fabs(mass) * g);
+        }
         int iters = 0;
-        int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s);
+        int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s, degree);
         inner_total += iters;
         if (rc != OV_OK && rc != OV_ERR_NOT_CONVERGED) {
             status = rc;
@@ -1389,7 +1443,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             count_launch();
             CKL();
         }
-        TRY(overlap_op<R>(c, Ysum, Srhs, mass, true, E, s));
+        TRY(overlap_op<R>(c, Ysum, Srhs, mass, true, E, s, degree));
         if (std::is_same<R, double>::value)
             CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
         else
@@ -1401,8 +1455,9 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         {
             double worst = 0.0;
             for (int j = 0; j < nrhs; ++j) worst = std::max(worst, res[j]);
-            char buf[96];
-            snprintf(buf, sizeof(buf), " | cycle %d: %d inner, %d systems, residual %.2e", outer, iters, ns, worst);
+            char buf[128];
+            snprintf(buf, sizeof(buf), " | cycle %d: n %d, %d inner, %d systems, residual %.2e", outer,
+                     degree > 0 ? degree : c->p.poly_degree, iters, ns, worst);
             hist += buf;
         }
     }

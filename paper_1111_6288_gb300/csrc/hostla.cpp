@@ -149,4 +149,23 @@ void host_chebyshev_coeffs_shifted_inverse_root(int n, double eps, double a, dou
     cheb_interp(n, eps, [a](double x) { return 1.0 / (a + std::sqrt(x)); }, out);
 }
 
+double host_poly_delta(const double* coeffs, int n, double eps) {
+    // max |1 - sqrt(x) P(x)| on a grid uniform in the Chebyshev angle (Clenshaw in FP64)
+    const int ng = 4096;
+    double worst = 0.0;
+    for (int q = 0; q <= ng; ++q) {
+        const double y = std::cos(3.141592653589793 * q / ng);
+        double b1 = 0.0, b2 = 0.0;
+        for (int k = n; k >= 1; --k) {
+            const double b0 = coeffs[k] + 2.0 * y * b1 - b2;
+            b2 = b1;
+            b1 = b0;
+        }
+        const double P = coeffs[0] + y * b1 - b2;
+        const double x = ((1.0 - eps) * y + 1.0 + eps) / 2.0;
+        worst = std::max(worst, std::fabs(1.0 - std::sqrt(x) * P));
+    }
+    return worst;
+}
+
 }  // namespace ovl

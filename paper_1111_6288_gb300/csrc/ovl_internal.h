@@ -170,5 +170,8 @@ void host_eigh(int n, std::vector<HostCplx>& A, std::vector<double>& w, std::vec
 void host_chebyshev_coeffs(int n, double eps, double* out);
 // The same for 1/(a + sqrt(x)), a > 0.
 void host_chebyshev_coeffs_shifted_inverse_root(int n, double eps, double a, double* out);
+// delta = max over [eps, 1] of |1 - sqrt(x) P(x)| for P = sum_k coeffs[k] T_k(y) (Sec. 2, eq. 2),
+// on a grid of 4097 points uniform in the Chebyshev angle.
+double host_poly_delta(const double* coeffs, int n, double eps);
 
 }  // namespace ovl

@@ -269,6 +269,36 @@ def test_solve_reaches_tolerance_and_matches_oracle(P, lat4, inner):
     ctx.close()
 
 
+@pytest.mark.parametrize("mass", [0.1, 0.02])
+def test_adaptive_order_solve_matches_oracle(P, lat4, mass):
+    """Mixed solve with the per-cycle polynomial degree (adaptive order): the true residual,
+    always taken at the full degree, reaches the tolerance against the oracle's operator, and
+    the inner cycles ran at lower degrees."""
+    import torch
+
+    d = lat4
+    degree, eps, tol = 200, EPS4, 1e-10
+    ctx = P.Context(P.Params(dims=d["dims"], bc=d["bc"], m0=M0, eps=eps, poly_degree=degree, precision=1,
+                             inner_precision=1, max_nrhs=4, adaptive_order=1))
+    ctx.set_gauge(to_dev(d["U"]))
+    P.deflate(ctx, to_dev(d["V"]), d["lam"])
+    b = synth.point_sources(d["dims"], [(0, 1), (3, 2)])
+    bd = to_dev(b)
+    xd = torch.zeros_like(bd)
+    st = P.solve_overlap(ctx, bd, xd, mass, tol=tol)
+    x = xd.cpu().numpy()
+    assert st.true_residual <= tol
+    small = ov.SmallSpace.from_eigenpairs(d["V"], d["lam"])
+    p = oracle_params(d, degree, eps)
+    for j in range(2):
+        r = b[j] - ov.overlap(d["U"], x[j], mass, p, small)
+        assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol
+    degrees = [int(t.split("n ")[1].split(",")[0]) for t in ctx.last_info.split("|")[1:]]
+    print(f"adaptive order, m = {mass}: cycles at degrees {degrees}; {ctx.last_info}")
+    assert min(degrees) < degree
+    ctx.close()
+
+
 def test_eigensolver_matches_dense(P, lat4):
     d = lat4
     ctx = make_ctx(P, d["dims"], d["bc"])

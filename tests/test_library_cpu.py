@@ -118,6 +118,26 @@ def test_library_polynomial_delta_matches_oracle(ovl, n, eps):
     ctx.close()
 
 
+@pytest.mark.parametrize("n,eps", [(8, 0.1), (64, 0.01), (300, 4e-4)])
+def test_poly_delta_of_any_degree_matches_oracle(ovl, n, eps):
+    want = chebyshev.approximation_error(chebyshev.chebyshev_coeffs(n, eps), eps)
+    assert ovl.poly_delta(n, eps) == pytest.approx(want, rel=0.05)
+
+
+def test_adaptive_degree_is_the_lowest_meeting_the_target(ovl):
+    ctx = ovl.Context(ovl.Params(dims=(4, 4, 4, 4), eps=4e-4, poly_degree=527))
+    for target in [1e-3, 3e-6, 1e-8, 5e-10]:
+        n = ctx.adaptive_degree(target)
+        assert n % 8 == 0 and n < 527
+        assert ovl.poly_delta(n, 4e-4) <= target < ovl.poly_delta(n - 8, 4e-4)
+    assert ctx.adaptive_degree(1e-10) == 527  # below the full degree's own delta (2.3e-10)
+    ctx.close()
+    custom = ovl.Context(ovl.Params(dims=(4, 4, 4, 4), eps=0.01, poly_degree=32,
+                                    coeffs=list(chebyshev.chebyshev_coeffs(32, 0.01))))
+    assert custom.adaptive_degree(1e-2) == 32  # the caller's coefficients are never replaced
+    custom.close()
+
+
 def _raw_ctx(ovl, **kw):
     p = ovl._ovl._Params()
     p.dims[:] = list(kw.get("dims", (4, 4, 4, 4)))
