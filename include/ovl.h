@@ -264,6 +264,24 @@ int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_ite
 int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, void* x,
                   int nrhs, double tol, ov_solve_stats* stats, ov_stream_t stream);
 
+/* Low modes of D_ov for the CG deflation of solve_overlap (Sec. 3.2: the paper deflates its CG
+ * with the D_ov eigensystem).  Computes the n_ev lowest eigenpairs of the chiral-sector operator
+ * A0 = P_s [2 (1 + s sign(H_w))] P_s = P_s D_ov^+ D_ov P_s, s = chirality (+1 or -1), at the field
+ * phase (a small-space bank must be registered for a non-zero phase): thick-restart Lanczos with
+ * full reorthogonalisation on FP32 sign applications, bases of krylov vectors (<= 0:
+ * max(3 n_ev, n_ev + 32); at least n_ev + 16), restarted from the lowest n_ev + max(8, n_ev/2)
+ * Ritz vectors until the n_ev lowest Ritz residual estimates are <= tol (<= 0: 1e-4) or
+ * max_restarts restarts ran (< 0: 50), then Rayleigh-Ritz with A0 applied to the Ritz vectors.  The space (FP32, n_ev vectors and A0
+ * applied to them) is registered for (phase, chirality), replacing an earlier one; from then on
+ * the FP32 inner CG of solve_overlap starts each system of that phase and chirality from the
+ * Galerkin solution on it and keeps its search directions A-orthogonal to it (deflated CG), for
+ * any mass (A(m) = (1 - m^2/4) A0 + m^2).  theta_out, res_out: host [n_ev] Ritz values of A0
+ * (ascending) and residual norms |A0 w - theta w|, or NULL.  Synchronises stream. */
+int ov_eigensolve_overlap(ov_ctx* ctx, double phase, int chirality, int n_ev, int krylov, double tol,
+                          int max_restarts, double* theta_out, double* res_out, ov_stream_t stream);
+/* Drop the D_ov deflation spaces of a phase (chirality +1, -1, or 0 for both). */
+int ov_clear_overlap_deflation(ov_ctx* ctx, double phase, int chirality);
+
 /* ---- derivatives with respect to the field (Sec. 4) --------------------- */
 /* The background field enters as the phase exp(i phi t) on the x links, phi = q E.  The
  * paper takes energy shifts from correlators at several field values; these calls give

@@ -32,8 +32,10 @@ from ._ovl import (  # noqa: F401
     chebyshev_coeffs,
     correlator,
     correlator_jacobian,
+    clear_overlap_deflation,
     deflate,
     eigensolve_Q,
+    eigensolve_overlap,
     host_eigh,
     inner,
     launch_count,

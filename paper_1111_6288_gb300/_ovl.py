@@ -75,6 +75,8 @@ _SIGNATURES = {
     "ov_last_info": (C.c_char_p, [_VP]),
     "ov_tune_info": (C.c_char_p, [_VP]),
     "ov_sync": (_I, [_VP, _VP]),
+    "ov_eigensolve_overlap": (_I, [_VP, _D, _I, _I, _I, _D, _I, _DP, _DP, _VP]),
+    "ov_clear_overlap_deflation": (_I, [_VP, _D, _I]),
     "ov_volume": (C.c_longlong, [_VP]),
     "ov_hw_norm": (_D, [_VP]),
     "ov_poly_delta": (_D, [_VP]),
@@ -308,6 +310,22 @@ def apply_wilson(ctx: Context, x, out, phase=None, hermitian=False, stream=None)
                             _stream(stream))
     _check(rc, ctx.handle)
     return out
+
+
+def eigensolve_overlap(ctx: Context, n_ev, chirality=1, phase=0.0, krylov=0, tol=1e-4, max_restarts=50, stream=None):
+    """Low modes of D_ov in one chiral sector for the solver's deflated CG (registered on ctx);
+    returns (Ritz values of P_s D_ov^+ D_ov P_s, residual norms) as numpy arrays."""
+    theta = np.zeros(n_ev)
+    res = np.zeros(n_ev)
+    _check(lib().ov_eigensolve_overlap(ctx.handle, float(phase), int(chirality), int(n_ev), int(krylov), float(tol),
+                                       int(max_restarts), theta.ctypes.data_as(_DP), res.ctypes.data_as(_DP),
+                                       _stream(stream)), ctx.handle)
+    return theta, res
+
+
+def clear_overlap_deflation(ctx: Context, phase=0.0, chirality=0):
+    """Drop the D_ov deflation spaces of a phase (chirality 0: both sectors)."""
+    _check(lib().ov_clear_overlap_deflation(ctx.handle, float(phase), int(chirality)), ctx.handle)
 
 
 def sync(ctx: Context, stream=None):

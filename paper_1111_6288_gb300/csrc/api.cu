@@ -49,6 +49,22 @@ struct Buf {
     size_t bytes = 0;
 };
 
+// Low modes of D_ov for the CG deflation of the solver (Sec. 3.2): Ritz pairs of the chiral-sector
+// operator A0 = P_s [2 (1 + s sign(H_w))] P_s = P_s D_ov^+ D_ov P_s at one field phase.  The inner
+// CG's operator at mass m is A(m) = (1 - m^2/4) A0 + m^2 on the sector, so one space serves every
+// mass.  FP32 vectors in the internal layout.
+struct DefSpace {
+    double phase = 0.0;
+    int chi = 1;
+    int n = 0;
+    void* W = nullptr;    // [n] orthonormal vectors of sector chi
+    void* AW0 = nullptr;  // A0 W
+    void* AWm = nullptr;  // A(m) W for the mass below
+    double mass = -1.0;   // mass of AWm and Einv (-1: not prepared)
+    std::vector<HostCplx> Einv;  // (W^+ A(m) W)^{-1}, n x n column-major
+    std::vector<double> theta, res;  // Ritz values of A0 and residual norms |A0 w - theta w|
+};
+
 }  // namespace
 
 struct ov_ctx {
@@ -68,6 +84,7 @@ struct ov_ctx {
     void* U16 = nullptr;  // 16-bit links of an FP16 / BF16 context
     bool gauge_set = false;
     std::vector<Bank> banks;
+    std::vector<DefSpace> dspaces;  // D_ov deflation spaces per (phase, chirality)
     std::map<std::string, Buf> ws;
     double2* d_partial = nullptr;
     long long partial_cap = 0;
@@ -919,6 +936,9 @@ int ov_destroy(ov_ctx* c) {
         if (b.d_signs) cudaFree(b.d_signs);
         if (b.Uh64) cudaFree(b.Uh64);
     }
+    for (auto& sp : c->dspaces)
+        for (void* q : {sp.W, sp.AW0, sp.AWm})
+            if (q) cudaFree(q);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& v : c->prof_events)
@@ -1205,6 +1225,253 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
 
 namespace {
 
+// ---- D_ov low modes and the deflated inner CG (Sec. 3.2) ----------------------------
+
+DefSpace* find_dspace(ov_ctx* c, double phase, int chi) {
+    for (auto& sp : c->dspaces)
+        if (sp.phase == phase && sp.chi == chi && sp.n > 0) return &sp;
+    return nullptr;
+}
+
+// Epilogue of the chiral-sector operator A(m) = P_s [k1 (1 + s sign) + m^2] P_s, k1 = 2 (1 - m^2/4),
+// applied to v (one sign application per system; the systems' chiralities in c->d_chi).
+Epilogue sector_operator(const ov_ctx* c, double mass, const void* v) {
+    const double k1 = 2.0 * (1.0 - 0.25 * mass * mass);
+    Epilogue fin;
+    fin.c_op = k1 / c->hw_norm;
+    fin.c1 = k1;
+    fin.chi = c->d_chi;
+    fin.c2 = k1 + mass * mass;
+    fin.v2 = v;
+    return fin;
+}
+
+// A(m) W = (1 - m^2/4) A0 W + m^2 W and (W^+ A(m) W)^{-1} for this mass (kept until the mass changes).
+int dspace_prepare(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s) {
+    if (sp.mass == mass && sp.AWm) return OV_OK;
+    const int n = sp.n;
+    const long long n12 = 12LL * c->g.V;
+    if (!sp.AWm && cudaMalloc(&sp.AWm, vec_bytes(c, OV_PREC_F32) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "deflation space: allocation of %d vectors failed", n);
+    }
+    std::vector<double> a(n, 1.0 - 0.25 * mass * mass), m2(n, mass * mass);
+    CK(cudaMemcpyAsync(sp.AWm, sp.W, vec_bytes(c, OV_PREC_F32) * n, cudaMemcpyDeviceToDevice, s));
+    launch_axpby<float>(a.data(), sp.AW0, m2.data(), sp.AWm, n12, n, s);
+    CKL();
+    std::vector<HostCplx> E, Rm;
+    TRY(gram_host<float>(c, sp.W, n, sp.AWm, n, E, s));
+    hermitize(E, n);
+    if (!host_cholesky(n, E)) return fail(c, OV_ERR_BREAKDOWN, "deflation space: W^+ A W not positive definite");
+    host_inv_lower_dag(n, E, Rm);  // Rm = L^{-+}, E^{-1} = Rm Rm^+
+    sp.Einv.assign((size_t)n * n, HostCplx{0, 0});
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const HostCplx x = Rm[i + (size_t)k * n], y = Rm[j + (size_t)k * n];  // x * conj(y)
+                re += x.re * y.re + x.im * y.im;
+                im += x.im * y.re - x.re * y.im;
+            }
+            sp.Einv[i + (size_t)j * n] = HostCplx{re, im};
+        }
+    sp.mass = mass;
+    return OV_OK;
+}
+
+// out (host, n) = Einv * (A_i^+ v for the n vectors A of the space), A = AWm or W.
+int dspace_coeffs(ov_ctx* c, DefSpace& sp, const void* A, const void* v, std::vector<HostCplx>& out, bool apply_einv,
+                  cudaStream_t s) {
+    std::vector<HostCplx> g;
+    TRY(gram_host<float>(c, A, sp.n, v, 1, g, s));
+    if (!apply_einv) {
+        out = g;
+        return OV_OK;
+    }
+    const int n = sp.n;
+    out.assign(n, HostCplx{0, 0});
+    for (int i = 0; i < n; ++i) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const HostCplx e = sp.Einv[i + (size_t)k * n], x = g[k];
+            re += e.re * x.re - e.im * x.im;
+            im += e.re * x.im + e.im * x.re;
+        }
+        out[i] = HostCplx{re, im};
+    }
+    return OV_OK;
+}
+
+// out = X + sign * sum_i A_i coef_i (one vector; out must not alias X).
+int dspace_combine(ov_ctx* c, const void* A, int n, const std::vector<HostCplx>& coef, double sign, const void* X,
+                   void* out, cudaStream_t s) {
+    std::vector<HostCplx> M(n);
+    for (int i = 0; i < n; ++i) M[i] = HostCplx{sign * coef[i].re, sign * coef[i].im};
+    const long long n12 = 12LL * c->g.V;
+    TRY(ensure_small(c, n, 0, 1));
+    std::vector<double2> tmp(n);
+    for (int i = 0; i < n; ++i) tmp[i] = make_double2(M[i].re, M[i].im);
+    CK(cudaMemcpyAsync(c->d_C, tmp.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, s));
+    combine<float>(A, n12, n, c->d_C, 1, 1, X ? 1.0 : 0.0, X, n12, out, n12, n12, s);
+    CKL();
+    return OV_OK;
+}
+
+// Thick-restart Lanczos with full reorthogonalisation on A0 in sector chi at the phase (FP32 sign
+// applications): Krylov bases of K vectors; after each pass the projected matrix (from the
+// reorthogonalisation coefficients) gives Ritz pairs, and the lowest `keep` Ritz vectors plus the
+// next Lanczos vector start the next pass, until the n_ev lowest Ritz estimates |beta y_K| are
+// below tol or max_restarts passes ran.  Then Rayleigh-Ritz with A0 applied to the n_ev Ritz
+// vectors; registers the space for (phase, chi).
+int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double tol, int max_restarts,
+                    cudaStream_t s) {
+    const int V = c->g.V;
+    const long long n12 = 12LL * V;
+    const size_t vb = vec_bytes(c, OV_PREC_F32);
+    const int keep = std::min(n_ev + std::max(8, n_ev / 2), K - 8);
+    if (keep < n_ev) return fail(c, OV_ERR_ARG, "krylov = %d too small for n_ev = %d (needs >= n_ev + 8)", K, n_ev);
+    void *Q, *w, *t, *r64, *Qr;
+    TRY(workspace(c, "lz_Q", OV_PREC_F32, K + 1, &Q));
+    TRY(workspace(c, "lz_Qr", OV_PREC_F32, keep, &Qr));
+    TRY(workspace(c, "lz_w", OV_PREC_F32, 1, &w));
+    TRY(workspace(c, "lz_t", OV_PREC_F32, 1, &t));
+    TRY(workspace(c, "lz_r64", OV_PREC_F64, 1, &r64));
+    SysSet S1;
+    S1.n = 1;
+    S1.phase = {phase};
+    S1.chi = {(signed char)chi};
+    TRY(ensure_small(c, (long long)(K + 1) * std::max(K, n_ev), (long long)(K + 1) * 4 * 152, std::max(n_ev, 1)));
+    // start: a random vector of the sector, normalised
+    random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)r64, n12, 0x1a2c3e5dULL + (unsigned long long)(chi + 2));
+    count_launch();
+    launch_convert<double, float>(r64, t, V, 1, s);
+    const int zero = 0;
+    CK(cudaMemcpyAsync(c->d_idx, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    const signed char ch = (signed char)chi;
+    CK(cudaMemcpyAsync(c->d_chi, &ch, 1, cudaMemcpyHostToDevice, s));
+    launch_chiral_split<float>(t, w, c->d_idx, c->d_chi, V, 1, s);
+    CKL();
+    double nrm2 = 0.0;
+    norm2_rhs<float>(w, n12, 1, &nrm2, c->d_partial, c->d_red, s);
+    launch_scale<float>(1.0 / std::sqrt(nrm2), w, Q, n12, s);
+    std::vector<HostCplx> H((size_t)K * K, HostCplx{0, 0}), T, Y;  // H: projections, column-major
+    std::vector<double> th, kept_theta;
+    int kb = 0, passes = 0, steps = 0;
+    double last_b = 0.0, worst_est = 0.0;
+    for (;;) {
+        for (int j = kb; j < K; ++j) {
+            char* qj = (char*)Q + (size_t)j * vb;
+            TRY(sign_pipeline<float>(c, qj, S1, false, sector_operator(c, 0.0, qj), w, s));
+            ++steps;
+            // w -= Q_{0..j} (Q^+ w), twice; the coefficients are column j of Q^+ A0 Q
+            std::vector<HostCplx> gsum(j + 1, HostCplx{0, 0});
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<HostCplx> g;
+                TRY(gram_host<float>(c, Q, j + 1, w, 1, g, s));
+                TRY(dspace_combine(c, Q, j + 1, g, -1.0, w, t, s));
+                std::swap(w, t);
+                for (int i = 0; i <= j; ++i) {
+                    gsum[i].re += g[i].re;
+                    gsum[i].im += g[i].im;
+                }
+            }
+            for (int i = 0; i <= j; ++i) H[i + (size_t)j * K] = gsum[i];
+            double b2 = 0.0;
+            norm2_rhs<float>(w, n12, 1, &b2, c->d_partial, c->d_red, s);
+            last_b = std::sqrt(b2);
+            if (!std::isfinite(last_b)) return fail(c, OV_ERR_NAN, "D_ov Lanczos: NaN at step %d", steps);
+            if (!(last_b > 0.0)) return fail(c, OV_ERR_BREAKDOWN, "D_ov Lanczos: invariant subspace at step %d", steps);
+            launch_scale<float>(1.0 / last_b, w, (char*)Q + (size_t)(j + 1) * vb, n12, s);
+            CKL();
+        }
+        ++passes;
+        // Hermitian projected matrix: kept Ritz values on the leading diagonal, the rest from the
+        // columns computed in this pass
+        T.assign((size_t)K * K, HostCplx{0, 0});
+        for (int j = 0; j < K; ++j) {
+            if (j < kb) T[j + (size_t)j * K] = HostCplx{kept_theta[j], 0.0};
+            else T[j + (size_t)j * K] = HostCplx{H[j + (size_t)j * K].re, 0.0};
+            for (int i = 0; i < j; ++i) {
+                if (j < kb) continue;  // the kept block is diagonal
+                const HostCplx h = H[i + (size_t)j * K];
+                T[i + (size_t)j * K] = h;
+                T[j + (size_t)i * K] = HostCplx{h.re, -h.im};
+            }
+        }
+        host_eigh(K, T, th, Y);
+        worst_est = 0.0;
+        for (int i = 0; i < n_ev; ++i) {
+            const HostCplx y = Y[(K - 1) + (size_t)i * K];
+            worst_est = std::max(worst_est, last_b * std::sqrt(y.re * y.re + y.im * y.im));
+        }
+        if (worst_est <= tol || passes > max_restarts) break;
+        // restart: Q[0..keep) = Q Y[:, 0..keep), Q[keep] = the next Lanczos vector
+        std::vector<HostCplx> Yk(Y.begin(), Y.begin() + (size_t)K * keep);
+        TRY(rotate<float>(c, Q, K, Yk, keep, Qr, s));
+        CK(cudaMemcpyAsync(Q, Qr, vb * keep, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync((char*)Q + (size_t)keep * vb, (char*)Q + (size_t)K * vb, vb, cudaMemcpyDeviceToDevice, s));
+        kept_theta.assign(th.begin(), th.begin() + keep);
+        kb = keep;
+        std::fill(H.begin(), H.end(), HostCplx{0, 0});
+    }
+    Y.resize((size_t)K * n_ev);  // the n_ev lowest Ritz vectors of the last pass
+    DefSpace* sp = find_dspace(c, phase, chi);
+    if (!sp) {
+        c->dspaces.push_back(DefSpace());
+        sp = &c->dspaces.back();
+        sp->phase = phase;
+        sp->chi = chi;
+    }
+    for (void** q : {&sp->W, &sp->AW0, &sp->AWm})
+        if (*q) {
+            CK(cudaStreamSynchronize(s));
+            CK(cudaFree(*q));
+            *q = nullptr;
+        }
+    sp->n = 0;
+    sp->mass = -1.0;
+    if (cudaMalloc(&sp->W, vb * n_ev) != cudaSuccess || cudaMalloc(&sp->AW0, vb * n_ev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "deflation space: allocation of %d vectors failed", n_ev);
+    }
+    TRY(rotate<float>(c, Q, K, Y, n_ev, sp->W, s));
+    void* tmp;
+    TRY(workspace(c, "lz_tmp", OV_PREC_F32, n_ev, &tmp));
+    TRY(cholqr2<float>(c, sp->W, n_ev, tmp, s));
+    // Rayleigh-Ritz with A0 on the Ritz vectors
+    SysSet Sn;
+    Sn.n = n_ev;
+    Sn.phase.assign(n_ev, phase);
+    Sn.chi.assign(n_ev, (signed char)chi);
+    TRY(sign_pipeline<float>(c, sp->W, Sn, false, sector_operator(c, 0.0, sp->W), sp->AW0, s));
+    std::vector<HostCplx> Hr, Z;
+    TRY(gram_host<float>(c, sp->W, n_ev, sp->AW0, n_ev, Hr, s));
+    hermitize(Hr, n_ev);
+    host_eigh(n_ev, Hr, sp->theta, Z);
+    TRY(rotate<float>(c, sp->W, n_ev, Z, n_ev, tmp, s));
+    CK(cudaMemcpyAsync(sp->W, tmp, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    TRY(rotate<float>(c, sp->AW0, n_ev, Z, n_ev, tmp, s));
+    CK(cudaMemcpyAsync(sp->AW0, tmp, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    // residuals |A0 w_i - theta_i w_i|
+    std::vector<double> mth(n_ev), ones(n_ev, 1.0);
+    for (int i = 0; i < n_ev; ++i) mth[i] = -sp->theta[i];
+    CK(cudaMemcpyAsync(tmp, sp->AW0, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    launch_axpby<float>(mth.data(), sp->W, ones.data(), tmp, n12, n_ev, s);
+    CKL();
+    sp->res.assign(n_ev, 0.0);
+    norm2_rhs<float>(tmp, n12, n_ev, sp->res.data(), c->d_partial, c->d_red, s);
+    for (double& r : sp->res) r = std::sqrt(r);
+    sp->n = n_ev;
+    char buf[256];
+    double worst = 0.0;
+    for (double r : sp->res) worst = std::max(worst, r);
+    snprintf(buf, sizeof(buf), "D_ov low modes: phase %.6g, chirality %+d, %d Lanczos steps in %d passes of %d, %d Ritz "
+             "pairs in [%.3e, %.3e], worst residual %.2e (estimate %.2e)", phase, chi, steps, passes, K, n_ev,
+             sp->theta.front(), sp->theta.back(), worst, worst_est);
+    c->info = buf;
+    return OV_OK;
+}
+
 // CG on the chiral-sector normal operator A_s = P_s [2 (1 - m^2/4)(1 + s sign) + m^2] P_s for each
 // system (rhs vector B_k in sector chi_k), in precision R.  Y: solutions, in the order of S.
 // Converged systems leave the batch: the active ones are kept at the front (a converged
@@ -1235,6 +1502,29 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
     std::vector<double2> pap(ns);
     norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
     b2 = rr;
+    // Deflation with the D_ov low modes of each system's (phase, chirality) (FP32): start from the
+    // Galerkin solution on the space, y = W E^-1 W^+ b (E = W^+ A W), and keep the search
+    // directions A-orthogonal to it, p = r + beta p - W E^-1 (A W)^+ r (deflated CG).
+    std::vector<DefSpace*> dsp(ns, nullptr);
+    bool any_defl = false;
+    if constexpr (std::is_same<R, float>::value) {
+        for (int k = 0; k < ns; ++k) {
+            DefSpace* sp = S0.chi.empty() ? nullptr : find_dspace(c, S0.phase[k], S0.chi[k]);
+            if (!sp || !(rr[k] > 0.0)) continue;
+            TRY(dspace_prepare(c, *sp, mass, s));
+            char* bk = (char*)B + (size_t)k * vb;
+            char* rk = (char*)r + (size_t)k * vb;
+            std::vector<HostCplx> dco, mu;
+            TRY(dspace_coeffs(c, *sp, sp->W, bk, dco, true, s));
+            TRY(dspace_combine(c, sp->W, sp->n, dco, 1.0, nullptr, (char*)Y + (size_t)k * vb, s));
+            TRY(dspace_combine(c, sp->AWm, sp->n, dco, -1.0, bk, rk, s));
+            TRY(dspace_coeffs(c, *sp, sp->AWm, rk, mu, true, s));
+            TRY(dspace_combine(c, sp->W, sp->n, mu, -1.0, rk, (char*)p + (size_t)k * vb, s));
+            dsp[k] = sp;
+            any_defl = true;
+        }
+        if (any_defl) norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
+    }
     auto swap_vec = [&](void* base, int i, int j) -> int {
         char* bi = (char*)base + (size_t)i * vb;
         char* bj = (char*)base + (size_t)j * vb;
@@ -1256,6 +1546,7 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
             std::swap(tol_rel[k], tol_rel[last]);
             std::swap(S.phase[k], S.phase[last]);
             std::swap(S.chi[k], S.chi[last]);
+            std::swap(dsp[k], dsp[last]);
         }
         --na;
         return OV_OK;
@@ -1293,7 +1584,23 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
             beta[k] = rr_new[k] / rr[k];
             rr[k] = rr_new[k];
         }
-        launch_axpby<R>(ones.data(), r, beta.data(), p, n12, na, s);  // p = r + beta p
+        if (!any_defl) {
+            launch_axpby<R>(ones.data(), r, beta.data(), p, n12, na, s);  // p = r + beta p
+        } else {
+            for (int k = 0; k < na; ++k) {
+                char* rk = (char*)r + (size_t)k * vb;
+                char* pk = (char*)p + (size_t)k * vb;
+                const void* dir = rk;
+                if (dsp[k]) {  // r - W E^-1 (A W)^+ r
+                    std::vector<HostCplx> mu;
+                    TRY(dspace_coeffs(c, *dsp[k], dsp[k]->AWm, rk, mu, true, s));
+                    char* tk = (char*)tmp + (size_t)k * vb;
+                    TRY(dspace_combine(c, dsp[k]->W, dsp[k]->n, mu, -1.0, rk, tk, s));
+                    dir = tk;
+                }
+                launch_axpby<R>(&ones[k], dir, &beta[k], pk, n12, 1, s);
+            }
+        }
         CKL();
         for (int k = na - 1; k >= 0; --k)
             if (std::sqrt(rr[k]) <= tol_rel[k] * std::sqrt(b2[k])) TRY(retire(k, na));
@@ -1496,6 +1803,45 @@ extern "C" int solve_overlap(ov_ctx* c, double mass, const double* phase, const 
     cudaStream_t s = (cudaStream_t)stream;
     return c->p.inner_precision == OV_PREC_F64 ? solve_impl<double>(c, mass, S, b, x, tol, stats, s)
                                                : solve_impl<float>(c, mass, S, b, x, tol, stats, s);
+}
+
+extern "C" int ov_eigensolve_overlap(ov_ctx* c, double phase, int chirality, int n_ev, int krylov, double tol,
+                                     int max_restarts, double* theta_out, double* res_out, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    if (!c->gauge_set) return fail(c, OV_ERR_STATE, "no gauge field set (call ov_set_gauge first)");
+    if (chirality != 1 && chirality != -1) return fail(c, OV_ERR_ARG, "chirality must be +1 or -1");
+    if (n_ev < 1 || n_ev > 256) return fail(c, OV_ERR_ARG, "n_ev = %d outside [1, 256]", n_ev);
+    if (!std::isfinite(phase)) return fail(c, OV_ERR_ARG, "non-finite phase");
+    const int K = krylov > 0 ? krylov : std::max(3 * n_ev, n_ev + 32);
+    if (K < n_ev + 16 || K > 2000) return fail(c, OV_ERR_ARG, "krylov = %d outside [n_ev + 16, 2000]", K);
+    if (phase != 0.0 && !find_bank(c, phase))
+        return fail(c, OV_ERR_NO_BANK, "no small-space bank registered for phase %.17g", phase);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(lanczos_overlap(c, phase, chirality, n_ev, K, tol > 0.0 ? tol : 1e-4, max_restarts >= 0 ? max_restarts : 50, s));
+    CK(cudaStreamSynchronize(s));
+    if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "D_ov Lanczos: a bounded device wait ran out");
+    const DefSpace* sp = find_dspace(c, phase, chirality);
+    for (int i = 0; i < n_ev; ++i) {
+        if (theta_out) theta_out[i] = sp->theta[i];
+        if (res_out) res_out[i] = sp->res[i];
+    }
+    return OV_OK;
+}
+
+extern "C" int ov_clear_overlap_deflation(ov_ctx* c, double phase, int chirality) {
+    if (!c) return OV_ERR_ARG;
+    for (auto& sp : c->dspaces)
+        if (sp.phase == phase && (chirality == 0 || sp.chi == chirality)) {
+            CK(cudaDeviceSynchronize());
+            for (void** q : {&sp.W, &sp.AW0, &sp.AWm})
+                if (*q) {
+                    CK(cudaFree(*q));
+                    *q = nullptr;
+                }
+            sp.n = 0;
+            sp.mass = -1.0;
+        }
+    return OV_OK;
 }
 
 // ============================================================================
