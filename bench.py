@@ -51,10 +51,10 @@ BC = (0, 0, 0, 1)  # periodic x, y, z; antiperiodic t
 METRIC = "D_ov applies/s, dslash HBM GB/s, time-to-1e-10 solve (mixed vs FP64)"
 UNIT = "D_ov applies/s"
 WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV}, m={MASS}, tol={TOL}"
-# ncu: DRAM bytes of the FP32 Wilson kernel over its algorithmic bytes on the bench lattice with warm
-# caches (plain and Clenshaw-epilogue launches, profiles/dslash_f32_16x16x16x32_warm_l2.md): the
-# loop's vectors and links stay in L2.  Set to None whenever the kernel changes until re-measured.
-DRAM_OVER_ALGORITHMIC = None
+# ncu, one pass, no replay, caches as the solve leaves them: DRAM bytes of the FP32 Wilson kernel
+# over its algorithmic bytes in the timed region of this bench (profiles/solve_16x32x32_launch_list.md):
+# the loop's vectors and links stay in L2.  Set to None whenever the kernel changes until re-measured.
+DRAM_OVER_ALGORITHMIC = 0.12
 
 
 def dist_env():

@@ -271,7 +271,10 @@ int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, 
  * full reorthogonalisation on FP32 sign applications, bases of krylov vectors (<= 0:
  * max(3 n_ev, n_ev + 32); at least n_ev + 16), restarted from the lowest n_ev + max(8, n_ev/2)
  * Ritz vectors until the n_ev lowest Ritz residual estimates are <= tol (<= 0: 1e-4) or
- * max_restarts restarts ran (< 0: 50), then Rayleigh-Ritz with A0 applied to the Ritz vectors.  The space (FP32, n_ev vectors and A0
+ * max_restarts restarts ran (< 0: 50), then Rayleigh-Ritz with A0 applied to the Ritz vectors,
+ * and D_ov^+ applied to them in FP64 (n_ev FP64 sign applications at the full degree): the
+ * solver keeps the space's share of each correction, D(m)^+ W c with c the Galerkin coefficients,
+ * in FP64, which removes the FP32 rounding of that large low-mode part.  The space (FP32, n_ev vectors and A0
  * applied to them) is registered for (phase, chirality), replacing an earlier one; from then on
  * the FP32 inner CG of solve_overlap starts each system of that phase and chirality from the
  * Galerkin solution on it and keeps its search directions A-orthogonal to it (deflated CG), for

@@ -63,6 +63,18 @@ struct DefSpace {
     double mass = -1.0;   // mass of AWm and Einv (-1: not prepared)
     std::vector<HostCplx> Einv;  // (W^+ A(m) W)^{-1}, n x n column-major
     std::vector<double> theta, res;  // Ritz values of A0 and residual norms |A0 w - theta w|
+    // FP64: W itself and D_ov^+ W, so that the solver adds the space's share of its correction,
+    // D(m)^+ W c, in FP64; DmW = D(m)^+ W for the mass dm_mass
+    void* W64 = nullptr;
+    void* DW64 = nullptr;
+    void* DmW64 = nullptr;
+    double dm_mass = -1.0;
+    // FP64 A0 W = 2 P_s D_ov^+ W (W lies in sector s, so gamma5 W = s W), A(m) W and
+    // (W^+ A(m) W)^{-1} in FP64: the solver takes the space's part of each sector residual with
+    // these before the FP32 CG sees it
+    void* AW64 = nullptr;
+    void* AWm64 = nullptr;
+    std::vector<HostCplx> Einv64;
 };
 
 }  // namespace
@@ -937,7 +949,7 @@ int ov_destroy(ov_ctx* c) {
         if (b.Uh64) cudaFree(b.Uh64);
     }
     for (auto& sp : c->dspaces)
-        for (void* q : {sp.W, sp.AW0, sp.AWm})
+        for (void* q : {sp.W, sp.AW0, sp.AWm, sp.W64, sp.DW64, sp.DmW64, sp.AW64, sp.AWm64})
             if (q) cudaFree(q);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1246,6 +1258,28 @@ Epilogue sector_operator(const ov_ctx* c, double mass, const void* v) {
     return fin;
 }
 
+int dspace_prepare_dm(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s);
+
+// Inverse of a Hermitian positive-definite matrix (column-major n x n; hermitised first).
+bool hpd_inverse(std::vector<HostCplx> E, int n, std::vector<HostCplx>& out) {
+    hermitize(E, n);
+    if (!host_cholesky(n, E)) return false;
+    std::vector<HostCplx> Rm;
+    host_inv_lower_dag(n, E, Rm);  // Rm = L^{-+}, E^{-1} = Rm Rm^+
+    out.assign((size_t)n * n, HostCplx{0, 0});
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const HostCplx x = Rm[i + (size_t)k * n], y = Rm[j + (size_t)k * n];  // x * conj(y)
+                re += x.re * y.re + x.im * y.im;
+                im += x.im * y.re - x.re * y.im;
+            }
+            out[i + (size_t)j * n] = HostCplx{re, im};
+        }
+    return true;
+}
+
 // A(m) W = (1 - m^2/4) A0 W + m^2 W and (W^+ A(m) W)^{-1} for this mass (kept until the mass changes).
 int dspace_prepare(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s) {
     if (sp.mass == mass && sp.AWm) return OV_OK;
@@ -1259,23 +1293,31 @@ int dspace_prepare(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s) {
     CK(cudaMemcpyAsync(sp.AWm, sp.W, vec_bytes(c, OV_PREC_F32) * n, cudaMemcpyDeviceToDevice, s));
     launch_axpby<float>(a.data(), sp.AW0, m2.data(), sp.AWm, n12, n, s);
     CKL();
-    std::vector<HostCplx> E, Rm;
+    std::vector<HostCplx> E;
     TRY(gram_host<float>(c, sp.W, n, sp.AWm, n, E, s));
-    hermitize(E, n);
-    if (!host_cholesky(n, E)) return fail(c, OV_ERR_BREAKDOWN, "deflation space: W^+ A W not positive definite");
-    host_inv_lower_dag(n, E, Rm);  // Rm = L^{-+}, E^{-1} = Rm Rm^+
-    sp.Einv.assign((size_t)n * n, HostCplx{0, 0});
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double re = 0.0, im = 0.0;
-            for (int k = 0; k < n; ++k) {
-                const HostCplx x = Rm[i + (size_t)k * n], y = Rm[j + (size_t)k * n];  // x * conj(y)
-                re += x.re * y.re + x.im * y.im;
-                im += x.im * y.re - x.re * y.im;
-            }
-            sp.Einv[i + (size_t)j * n] = HostCplx{re, im};
-        }
+    if (!hpd_inverse(E, n, sp.Einv)) return fail(c, OV_ERR_BREAKDOWN, "deflation space: W^+ A W not positive definite");
     sp.mass = mass;
+    return OV_OK;
+}
+
+// The FP64 counterparts for this mass: A(m) W = (1 - m^2/4) A0 W + m^2 W and (W^+ A(m) W)^{-1}.
+int dspace_prepare64(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s) {
+    if (sp.AWm64 && sp.dm_mass == mass && !sp.Einv64.empty()) return OV_OK;
+    const int n = sp.n;
+    const size_t b64 = vec_bytes(c, OV_PREC_F64) * n;
+    if (!sp.AWm64 && cudaMalloc(&sp.AWm64, b64) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "deflation space: allocation of %d FP64 vectors failed", n);
+    }
+    std::vector<double> a(n, 1.0 - 0.25 * mass * mass), m2(n, mass * mass);
+    CK(cudaMemcpyAsync(sp.AWm64, sp.W64, b64, cudaMemcpyDeviceToDevice, s));
+    launch_axpby<double>(a.data(), sp.AW64, m2.data(), sp.AWm64, 12LL * c->g.V, n, s);
+    CKL();
+    std::vector<HostCplx> E;
+    TRY(gram_host<double>(c, sp.W64, n, sp.AWm64, n, E, s));
+    if (!hpd_inverse(E, n, sp.Einv64))
+        return fail(c, OV_ERR_BREAKDOWN, "deflation space: W^+ A W (FP64) not positive definite");
+    TRY(dspace_prepare_dm(c, sp, mass, s));  // sets dm_mass
     return OV_OK;
 }
 
@@ -1302,7 +1344,8 @@ int dspace_coeffs(ov_ctx* c, DefSpace& sp, const void* A, const void* v, std::ve
     return OV_OK;
 }
 
-// out = X + sign * sum_i A_i coef_i (one vector; out must not alias X).
+// out = X + sign * sum_i A_i coef_i (one vector of precision R; out must not alias X).
+template <typename R = float>
 int dspace_combine(ov_ctx* c, const void* A, int n, const std::vector<HostCplx>& coef, double sign, const void* X,
                    void* out, cudaStream_t s) {
     std::vector<HostCplx> M(n);
@@ -1312,8 +1355,25 @@ int dspace_combine(ov_ctx* c, const void* A, int n, const std::vector<HostCplx>&
     std::vector<double2> tmp(n);
     for (int i = 0; i < n; ++i) tmp[i] = make_double2(M[i].re, M[i].im);
     CK(cudaMemcpyAsync(c->d_C, tmp.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, s));
-    combine<float>(A, n12, n, c->d_C, 1, 1, X ? 1.0 : 0.0, X, n12, out, n12, n12, s);
+    combine<R>(A, n12, n, c->d_C, 1, 1, X ? 1.0 : 0.0, X, n12, out, n12, n12, s);
     CKL();
+    return OV_OK;
+}
+
+// D(m)^+ W = (1 - m/2) D_ov^+ W + m W in FP64 for this mass.
+int dspace_prepare_dm(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s) {
+    if (!sp.DW64) return OV_OK;
+    if (sp.dm_mass == mass && sp.DmW64) return OV_OK;
+    const size_t b64 = vec_bytes(c, OV_PREC_F64) * sp.n;
+    if (!sp.DmW64 && cudaMalloc(&sp.DmW64, b64) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "deflation space: allocation of %d FP64 vectors failed", sp.n);
+    }
+    std::vector<double> a(sp.n, 1.0 - 0.5 * mass), mm(sp.n, mass);
+    CK(cudaMemcpyAsync(sp.DmW64, sp.W64, b64, cudaMemcpyDeviceToDevice, s));
+    launch_axpby<double>(a.data(), sp.DW64, mm.data(), sp.DmW64, 12LL * c->g.V, sp.n, s);
+    CKL();
+    sp.dm_mass = mass;
     return OV_OK;
 }
 
@@ -1422,7 +1482,7 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
         sp->phase = phase;
         sp->chi = chi;
     }
-    for (void** q : {&sp->W, &sp->AW0, &sp->AWm})
+    for (void** q : {&sp->W, &sp->AW0, &sp->AWm, &sp->W64, &sp->DW64, &sp->DmW64, &sp->AW64, &sp->AWm64})
         if (*q) {
             CK(cudaStreamSynchronize(s));
             CK(cudaFree(*q));
@@ -1430,6 +1490,7 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
         }
     sp->n = 0;
     sp->mass = -1.0;
+    sp->dm_mass = -1.0;
     if (cudaMalloc(&sp->W, vb * n_ev) != cudaSuccess || cudaMalloc(&sp->AW0, vb * n_ev) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, OV_ERR_OOM, "deflation space: allocation of %d vectors failed", n_ev);
@@ -1472,14 +1533,60 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
     return OV_OK;
 }
 
+// W in FP64 and D_ov^+ W (FP64 sign applications, the full degree) for the solver's FP64 share.
+int dspace_fp64(ov_ctx* c, DefSpace& sp, cudaStream_t s) {
+    for (void** q : {&sp.W64, &sp.DW64, &sp.DmW64})
+        if (*q) {
+            CK(cudaStreamSynchronize(s));
+            CK(cudaFree(*q));
+            *q = nullptr;
+        }
+    sp.dm_mass = -1.0;
+    const size_t b64 = vec_bytes(c, OV_PREC_F64) * sp.n;
+    if (cudaMalloc(&sp.W64, b64) != cudaSuccess || cudaMalloc(&sp.DW64, b64) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "deflation space: allocation of %d FP64 vectors failed", sp.n);
+    }
+    launch_convert<float, double>(sp.W, sp.W64, c->g.V, sp.n, s);
+    CKL();
+    SysSet S;
+    S.n = sp.n;
+    S.phase.assign(sp.n, sp.phase);
+    TRY(overlap_op<double>(c, sp.W64, S, 0.0, true, sp.DW64, s));
+    // A0 W = 2 P_s D_ov^+ W in FP64; the FP32 copy replaces the FP32-operator one
+    if (cudaMalloc(&sp.AW64, b64) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OV_ERR_OOM, "deflation space: allocation of %d FP64 vectors failed", sp.n);
+    }
+    std::vector<int> idx(sp.n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::vector<signed char> chis(sp.n, (signed char)sp.chi);
+    TRY(ensure_small(c, 0, 0, sp.n));
+    CK(cudaMemcpyAsync(c->d_idx, idx.data(), sizeof(int) * sp.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_chi, chis.data(), sp.n, cudaMemcpyHostToDevice, s));
+    void* t64;
+    TRY(workspace(c, "dsp_t64", OV_PREC_F64, sp.n, &t64));
+    launch_chiral_split<double>(sp.DW64, t64, c->d_idx, c->d_chi, c->g.V, sp.n, s);
+    launch_scale<double>(2.0, t64, sp.AW64, 12LL * c->g.V * sp.n, s);
+    launch_convert<double, float>(sp.AW64, sp.AW0, c->g.V, sp.n, s);
+    CKL();
+    sp.mass = -1.0;
+    sp.Einv64.clear();
+    return OV_OK;
+}
+
 // CG on the chiral-sector normal operator A_s = P_s [2 (1 - m^2/4)(1 + s sign) + m^2] P_s for each
 // system (rhs vector B_k in sector chi_k), in precision R.  Y: solutions, in the order of S.
 // Converged systems leave the batch: the active ones are kept at the front (a converged
 // system is swapped with the last active one), so later sign applications run only on
 // systems that still iterate; Y is put back in the original order at the end.
 template <typename R>
+// coef0 (optional): for each system whose space carries the FP64 part, the Galerkin start is
+// returned as coefficients c (y = W c + Y) instead of being added to Y in FP32: its size, about
+// |r| / lambda_min, would leave FP32 rounding of that order in Y.
 int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, const std::vector<double>& tol_rel0,
-             int max_iter, int* iters, cudaStream_t s, int degree = 0) {
+             int max_iter, int* iters, cudaStream_t s, int degree = 0,
+             std::vector<std::vector<HostCplx>>* coef0 = nullptr) {
     const int prec = prec_of<R>();
     const int ns = S0.n;
     const long long n12 = 12LL * c->g.V;
@@ -1516,7 +1623,8 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
             char* rk = (char*)r + (size_t)k * vb;
             std::vector<HostCplx> dco, mu;
             TRY(dspace_coeffs(c, *sp, sp->W, bk, dco, true, s));
-            TRY(dspace_combine(c, sp->W, sp->n, dco, 1.0, nullptr, (char*)Y + (size_t)k * vb, s));
+            if (coef0 && sp->DW64) (*coef0)[k] = dco;  // kept in FP64 by the caller
+            else TRY(dspace_combine(c, sp->W, sp->n, dco, 1.0, nullptr, (char*)Y + (size_t)k * vb, s));
             TRY(dspace_combine(c, sp->AWm, sp->n, dco, -1.0, bk, rk, s));
             TRY(dspace_coeffs(c, *sp, sp->AWm, rk, mu, true, s));
             TRY(dspace_combine(c, sp->W, sp->n, mu, -1.0, rk, (char*)p + (size_t)k * vb, s));
@@ -1703,6 +1811,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         // keep the non-zero sectors, compacted
         SysSet S;
         std::vector<double> tol_rel;
+        std::vector<int> rhs_of_sys;
         int ns = 0;
         for (int k = 0; k < ns0; ++k) {
             const int j = src[k];
@@ -1714,11 +1823,42 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             S.phase.push_back(Srhs.phase[j]);
             S.chi.push_back(chi[k]);
             sys_of_rhs[2 * j + (chi[k] > 0 ? 0 : 1)] = ns;
+            rhs_of_sys.push_back(j);
             const double want = 0.5 * tol * std::sqrt(bn2[j] / sn2[k]);
             tol_rel.push_back(std::min(0.5, std::max(base_tol, want)));
             ++ns;
         }
         S.n = ns;
+        // FP32 inner solves: each sector residual loses its part on the system's D_ov deflation
+        // space in FP64, r_s -= A W c with c = (W^+ A W)^{-1} W^+ r_s (A, W in FP64); the FP32
+        // CG then solves for the remainder, and W c enters the correction in FP64.
+        std::vector<std::vector<HostCplx>> c_low(ns);
+        if (std::is_same<R, float>::value) {
+            for (int k = 0; k < ns; ++k) {
+                DefSpace* sp = find_dspace(c, S.phase[k], S.chi[k]);
+                if (!sp || !sp->AW64) continue;
+                TRY(dspace_prepare64(c, *sp, mass, s));
+                char* rk = (char*)S64 + (size_t)k * vb64;
+                std::vector<HostCplx> g;
+                TRY(gram_host<double>(c, sp->W64, sp->n, rk, 1, g, s));
+                const int n = sp->n;
+                c_low[k].assign(n, HostCplx{0, 0});
+                for (int i = 0; i < n; ++i)
+                    for (int q = 0; q < n; ++q) {
+                        const HostCplx e = sp->Einv64[i + (size_t)q * n], x = g[q];
+                        c_low[k][i].re += e.re * x.re - e.im * x.im;
+                        c_low[k][i].im += e.re * x.im + e.im * x.re;
+                    }
+                void* t64;
+                TRY(workspace(c, "sol_t64", OV_PREC_F64, 1, &t64));
+                TRY(dspace_combine<double>(c, sp->AWm64, n, c_low[k], -1.0, rk, t64, s));
+                CK(cudaMemcpyAsync(rk, t64, vb64, cudaMemcpyDeviceToDevice, s));
+                double h2 = 0.0;
+                norm2_rhs<double>(rk, n12, 1, &h2, c->d_partial, c->d_red, s);
+                const int j = rhs_of_sys[k];
+                if (h2 > 0.0) tol_rel[k] = std::min(0.5, std::max(base_tol, 0.5 * tol * std::sqrt(bn2[j] / h2)));
+            }
+        }
         if (std::is_same<R, double>::value)
             CK(cudaMemcpyAsync(Bs, S64, vb64 * ns, cudaMemcpyDeviceToDevice, s));
         else
@@ -1735,7 +1875,16 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             degree = degree_for_delta(c, 0.5 * std::fabs(mass) * g);
         }
         int iters = 0;
-        int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s, degree);
+        std::vector<std::vector<HostCplx>> coef0(ns);
+        int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s, degree, &coef0);
+        for (int k = 0; k < ns; ++k) {
+            if (c_low[k].empty()) continue;
+            if (coef0[k].empty()) coef0[k].assign(c_low[k].size(), HostCplx{0, 0});
+            for (size_t i = 0; i < c_low[k].size(); ++i) {
+                coef0[k][i].re += c_low[k][i].re;
+                coef0[k][i].im += c_low[k][i].im;
+            }
+        }
         inner_total += iters;
         if (rc != OV_OK && rc != OV_ERR_NOT_CONVERGED) {
             status = rc;
@@ -1755,6 +1904,17 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
         else
             launch_convert<float, double>(E, E64, V, nrhs, s);
+        // the deflation spaces' share of the correction, D(m)^+ W c, in FP64
+        for (int k = 0; k < ns; ++k) {
+            if (coef0[k].empty()) continue;
+            DefSpace* sp = find_dspace(c, S.phase[k], S.chi[k]);
+            TRY(dspace_prepare_dm(c, *sp, mass, s));
+            void* t64;
+            TRY(workspace(c, "sol_t64", OV_PREC_F64, 1, &t64));
+            char* ej = (char*)E64 + (size_t)rhs_of_sys[k] * vb64;
+            TRY(dspace_combine<double>(c, sp->DmW64, sp->n, coef0[k], 1.0, ej, t64, s));
+            CK(cudaMemcpyAsync(ej, t64, vb64, cudaMemcpyDeviceToDevice, s));
+        }
         launch_axpby<double>(ones.data(), E64, ones.data(), X, n12, nrhs, s);
         CKL();
         ++outer;
@@ -1818,6 +1978,7 @@ extern "C" int ov_eigensolve_overlap(ov_ctx* c, double phase, int chirality, int
         return fail(c, OV_ERR_NO_BANK, "no small-space bank registered for phase %.17g", phase);
     cudaStream_t s = (cudaStream_t)stream;
     TRY(lanczos_overlap(c, phase, chirality, n_ev, K, tol > 0.0 ? tol : 1e-4, max_restarts >= 0 ? max_restarts : 50, s));
+    TRY(dspace_fp64(c, *find_dspace(c, phase, chirality), s));
     CK(cudaStreamSynchronize(s));
     if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "D_ov Lanczos: a bounded device wait ran out");
     const DefSpace* sp = find_dspace(c, phase, chirality);
@@ -1833,13 +1994,14 @@ extern "C" int ov_clear_overlap_deflation(ov_ctx* c, double phase, int chirality
     for (auto& sp : c->dspaces)
         if (sp.phase == phase && (chirality == 0 || sp.chi == chirality)) {
             CK(cudaDeviceSynchronize());
-            for (void** q : {&sp.W, &sp.AW0, &sp.AWm})
+            for (void** q : {&sp.W, &sp.AW0, &sp.AWm, &sp.W64, &sp.DW64, &sp.DmW64, &sp.AW64, &sp.AWm64})
                 if (*q) {
                     CK(cudaFree(*q));
                     *q = nullptr;
                 }
             sp.n = 0;
             sp.mass = -1.0;
+            sp.dm_mass = -1.0;
         }
     return OV_OK;
 }
