@@ -408,15 +408,15 @@ __global__ void multidot_sum_k(const double2* __restrict__ partial, int nchunk, 
 // out_j = alpha X_j + sum_i A_i C[i][j], up to CJ outputs per launch; the coefficients are
 // converted once to the data precision R in shared memory.
 constexpr int CJ = 8;
-template <typename R>
+template <typename R, int CJT>
 __global__ void __launch_bounds__(256) combine_k(const typename C2<R>::T* __restrict__ A, long long sA, int na,
                                                  const double2* __restrict__ C, int ldc, int j0, int nj, double alpha,
                                                  const typename C2<R>::T* __restrict__ X, long long sX,
                                                  typename C2<R>::T* __restrict__ out, long long sO, long long n) {
     extern __shared__ unsigned char cmb_raw[];
-    typename C2<R>::T* shC = (typename C2<R>::T*)cmb_raw;  // [na][CJ]
-    for (int q = threadIdx.x; q < na * CJ; q += blockDim.x) {
-        const int i = q / CJ, j = q % CJ;
+    typename C2<R>::T* shC = (typename C2<R>::T*)cmb_raw;  // [na][CJT]
+    for (int q = threadIdx.x; q < na * CJT; q += blockDim.x) {
+        const int i = q / CJT, j = q % CJT;
         const double2 c = (j < nj) ? C[(long long)i * ldc + j0 + j] : make_double2(0, 0);
         shC[q].x = (R)c.x;
         shC[q].y = (R)c.y;
@@ -424,14 +424,14 @@ __global__ void __launch_bounds__(256) combine_k(const typename C2<R>::T* __rest
     __syncthreads();
     const R al = (R)alpha;
     for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
-        R accr[CJ], acci[CJ];
+        R accr[CJT], acci[CJT];
 #pragma unroll
-        for (int j = 0; j < CJ; ++j) accr[j] = acci[j] = 0;
+        for (int j = 0; j < CJT; ++j) accr[j] = acci[j] = 0;
         for (int i = 0; i < na; ++i) {
             typename C2<R>::T a = A[(long long)i * sA + m];
 #pragma unroll
-            for (int j = 0; j < CJ; ++j) {
-                const typename C2<R>::T c = shC[i * CJ + j];
+            for (int j = 0; j < CJT; ++j) {
+                const typename C2<R>::T c = shC[i * CJT + j];
                 accr[j] += a.x * c.x - a.y * c.y;
                 acci[j] += a.x * c.y + a.y * c.x;
             }
@@ -708,9 +708,36 @@ void launch_gamma5(const void* x, void* y, int V, int nrhs, cudaStream_t s) {
     count_launch();
 }
 
+// C = A^+ B for nb <= NB columns through the row-dot kernel of the small-space projection (chunks of
+// at most 4096 elements, so that each lane's FP32 partial sum stays short).
+template <typename R, int NB>
+void multidot_few(const void* A, long long sA, int na, const void* B, long long sB, int nb, long long n, double2* d_C,
+                  double2* d_partial, long long partial_cap, cudaStream_t s) {
+    typedef typename C2<R>::T T;
+    const int rowblocks = (na + 63) / 64;
+    long long nchunk = std::max((4LL * 152 + rowblocks - 1) / rowblocks, (n + 4095) / 4096);
+    const long long cap = partial_cap / ((long long)na * nb);
+    if (nchunk > cap) nchunk = std::max(1LL, cap);
+    long long chunk = (n + nchunk - 1) / nchunk;
+    chunk = ((chunk + 31) / 32) * 32;
+    nchunk = (n + chunk - 1) / chunk;
+    dim3 grid((unsigned)nchunk, rowblocks);
+    vdot_rows_k<R, NB><<<grid, 256, 0, s>>>((const T*)A, sA, na, (const T*)B, sB, nb, n, chunk, d_partial);
+    count_launch();
+    const int nab = na * nb;
+    multidot_sum_k<<<(nab + 255) / 256, 256, 0, s>>>(d_partial, (int)nchunk, nab, d_C);
+    count_launch();
+}
+
 template <typename R>
 void multidot(const void* A, long long strideA, int na, const void* B, long long strideB, int nb, long long n,
               double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s) {
+    if (nb <= 4) {  // few columns: one warp per 8 rows, every element of A read once, no padded pairs
+        if (nb == 1) multidot_few<R, 1>(A, strideA, na, B, strideB, nb, n, d_C, d_partial, partial_cap, s);
+        else if (nb == 2) multidot_few<R, 2>(A, strideA, na, B, strideB, nb, n, d_C, d_partial, partial_cap, s);
+        else multidot_few<R, 4>(A, strideA, na, B, strideB, nb, n, d_C, d_partial, partial_cap, s);
+        return;
+    }
     const int ti = (na + MT - 1) / MT, tj = (nb + MT - 1) / MT;
     // enough chunks to fill the GPU about four times over, bounded by the partial buffer
     // enough chunks to fill the GPU, and chunks of at most 4096 elements (each thread's partial
@@ -734,10 +761,18 @@ void multidot(const void* A, long long strideA, int na, const void* B, long long
 template <typename R>
 void combine(const void* A, long long strideA, int na, const double2* d_C, int ldc, int nb, double alpha,
              const void* X, long long strideX, void* out, long long strideO, long long n, cudaStream_t s) {
+    if (nb == 1) {  // one column: no padding columns in the inner loop
+        const size_t shm1 = sizeof(typename C2<R>::T) * (size_t)na;
+        combine_k<R, 1><<<grid_for(n, 256, 152 * 8), 256, shm1, s>>>(
+            (const typename C2<R>::T*)A, strideA, na, d_C, ldc, 0, 1, alpha, (const typename C2<R>::T*)X, strideX,
+            (typename C2<R>::T*)out, strideO, n);
+        count_launch();
+        return;
+    }
     const size_t shm = sizeof(typename C2<R>::T) * (size_t)na * CJ;
     for (int j0 = 0; j0 < nb; j0 += CJ) {
         const int nj = (nb - j0 < CJ) ? nb - j0 : CJ;
-        combine_k<R><<<grid_for(n, 256, 152 * 8), 256, shm, s>>>(
+        combine_k<R, CJ><<<grid_for(n, 256, 152 * 8), 256, shm, s>>>(
             (const typename C2<R>::T*)A, strideA, na, d_C, ldc, j0, nj, alpha, (const typename C2<R>::T*)X, strideX,
             (typename C2<R>::T*)out, strideO, n);
         count_launch();
