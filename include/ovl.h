@@ -104,6 +104,10 @@ typedef struct ov_params {
                              | 8 for the FP32 register budget of 7 blocks per SM instead of 6,
                              | 16 for the kernel that stages x-rows in shared memory (used where
                              the lattice allows it, see ov_tune_info). */
+    int poly_kind;        /* coeffs = NULL: 0 = Chebyshev interpolant of x^{-1/2} (ov_chebyshev_coeffs),
+                             1 = the polynomial of least relative error max |1 - sqrt(x) P(x)|
+                             on [eps, 1] (Remez exchange, ov_minimax_coeffs; its delta follows
+                             eq. 2 with A ~ 0.41, where the interpolant's is ~2x larger) */
     int adaptive_order;   /* solve_overlap: 0 = every inner sign application at poly_degree;
                              1 = per outer cycle, the lowest degree (a multiple of 8) whose
                              interpolant has delta <= 0.5 m g, g = the cycle's inner tolerance
@@ -162,8 +166,14 @@ double ov_poly_delta(const ov_ctx* ctx);
 /* delta of the degree-n Chebyshev interpolant of x^{-1/2} on [eps, 1] (as ov_poly_delta, no
  * context needed); -1 for invalid arguments. */
 double ov_poly_delta_n(int n, double eps);
+/* out[0..n] = coefficients (T_k basis of y = (2x - 1 - eps)/(1 - eps)) of the degree-n
+ * polynomial P minimising max over [eps, 1] of |1 - sqrt(x) P(x)| (Sec. 2: the minimax
+ * approximation whose error eq. 2 describes), by the Remez exchange algorithm on the host;
+ * returns that delta, or -1 for invalid arguments (n in [0, 4000]). */
+double ov_minimax_coeffs(int n, double eps, double* out);
 /* The degree the adaptive order picks for a polynomial error target: the lowest multiple of 8
- * whose interpolant on the context's interval has delta <= delta_target, else poly_degree. */
+ * whose polynomial (of the context's poly_kind) on its interval has delta <= delta_target, else
+ * poly_degree. */
 int ov_adaptive_degree(ov_ctx* ctx, double delta_target);
 
 /* Turn event timing of the polynomial loops on (on != 0) or off. */

@@ -40,6 +40,7 @@ from ._ovl import (  # noqa: F401
     inner,
     launch_count,
     lib,
+    minimax_coeffs,
     library_path,
     pion_correlator,
     poly_delta,

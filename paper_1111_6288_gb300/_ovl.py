@@ -40,6 +40,7 @@ class _Params(C.Structure):
         ("max_iter", C.c_int),
         ("inner_tol", C.c_double),
         ("launch_shape", C.c_int),
+        ("poly_kind", C.c_int),
         ("adaptive_order", C.c_int),
     ]
 
@@ -81,6 +82,7 @@ _SIGNATURES = {
     "ov_hw_norm": (_D, [_VP]),
     "ov_poly_delta": (_D, [_VP]),
     "ov_poly_delta_n": (_D, [_I, _D]),
+    "ov_minimax_coeffs": (_D, [_I, _D, _DP]),
     "ov_adaptive_degree": (_I, [_VP, _D]),
     "ov_set_gauge": (_I, [_VP, _VP, _I, _VP]),
     "ov_set_profiling": (_I, [_VP, _I]),
@@ -162,6 +164,7 @@ class Params:
     max_iter: int = 0
     inner_tol: float = 0.0
     launch_shape: int = 0
+    poly_kind: int = 0
     adaptive_order: int = 0
 
 
@@ -195,6 +198,7 @@ class Context:
         p.max_iter = params.max_iter
         p.inner_tol = params.inner_tol
         p.launch_shape = params.launch_shape
+        p.poly_kind = params.poly_kind
         p.adaptive_order = params.adaptive_order
         h = C.c_void_p()
         rc = lib().ov_create(C.byref(p), C.byref(h))
@@ -414,6 +418,16 @@ def chebyshev_coeffs(n, eps):
     out = np.zeros(n + 1)
     _check(lib().ov_chebyshev_coeffs(int(n), float(eps), out.ctypes.data_as(_DP)))
     return out
+
+
+def minimax_coeffs(n, eps):
+    """The library's minimax coefficients (least relative error for x^{-1/2} on [eps, 1], host);
+    returns (coefficients, delta)."""
+    out = np.zeros(n + 1)
+    d = float(lib().ov_minimax_coeffs(int(n), float(eps), out.ctypes.data_as(_DP)))
+    if d < 0:
+        raise OvlError(1, "ov_minimax_coeffs: invalid arguments")
+    return out, d
 
 
 def poly_delta(n, eps):

@@ -249,14 +249,15 @@ Bank* find_bank(ov_ctx* c, double phase) {
     return nullptr;
 }
 
-// Coefficients of the degree-n interpolant of x^{-1/2} on the context's interval (n = poly_degree:
-// the context's own, which may be the caller's).
+// Coefficients of the degree-n polynomial of the context's kind (interpolant or minimax) on its
+// interval (n = poly_degree: the context's own, which may be the caller's).
 const std::vector<double>& coeffs_of(ov_ctx* c, int n) {
     if (n == c->p.poly_degree) return c->coeffs;
     auto it = c->coeff_sets.find(n);
     if (it == c->coeff_sets.end()) {
         std::vector<double> cf(n + 1);
-        host_chebyshev_coeffs(n, c->p.eps, cf.data());
+        if (c->p.poly_kind == 1) host_minimax_coeffs(n, c->p.eps, cf.data());
+        else host_chebyshev_coeffs(n, c->p.eps, cf.data());
         it = c->coeff_sets.emplace(n, std::move(cf)).first;
     }
     return it->second;
@@ -912,6 +913,9 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     if (p->max_nrhs < 1 || p->max_nrhs > kMaxRhs / 2)
         return fail(c, OV_ERR_ARG, "max_nrhs = %d outside [1, %d]", p->max_nrhs, kMaxRhs / 2);
     if (!std::isfinite(p->m0)) return fail(c, OV_ERR_ARG, "m0 not finite");
+    if (p->poly_kind != 0 && p->poly_kind != 1) return fail(c, OV_ERR_ARG, "poly_kind = %d invalid", p->poly_kind);
+    if (p->poly_kind == 1 && p->poly_degree > 4000)
+        return fail(c, OV_ERR_ARG, "poly_degree = %d above 4000 for the minimax polynomial", p->poly_degree);
     {
         const int rb = p->launch_shape & kShapeRhsMask;
         if (p->launch_shape < 0 || (p->launch_shape & ~(kShapeRhsMask | kShapeDense | kShapeTiled)) ||
@@ -927,6 +931,7 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     c->g.V = (int)V;
     c->coeffs.resize(p->poly_degree + 1);
     if (p->coeffs) std::copy(p->coeffs, p->coeffs + p->poly_degree + 1, c->coeffs.begin());
+    else if (p->poly_kind == 1) host_minimax_coeffs(p->poly_degree, p->eps, c->coeffs.data());
     else host_chebyshev_coeffs(p->poly_degree, p->eps, c->coeffs.data());
     c->p.coeffs = nullptr;
     c->hw_norm = p->hw_norm > 0.0 ? p->hw_norm : std::fabs(4.0 + p->m0) + 4.0;
@@ -991,6 +996,11 @@ double ov_poly_delta_n(int n, double eps) {
     std::vector<double> cf(n + 1);
     host_chebyshev_coeffs(n, eps, cf.data());
     return host_poly_delta(cf.data(), n, eps);
+}
+
+double ov_minimax_coeffs(int n, double eps, double* out) {
+    if (n < 0 || n > 4000 || !out || !(eps > 0.0 && eps < 1.0)) return -1.0;
+    return host_minimax_coeffs(n, eps, out);
 }
 
 int ov_adaptive_degree(ov_ctx* c, double delta_target) {

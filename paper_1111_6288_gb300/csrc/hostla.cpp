@@ -149,6 +149,137 @@ void host_chebyshev_coeffs_shifted_inverse_root(int n, double eps, double a, dou
     cheb_interp(n, eps, [a](double x) { return 1.0 / (a + std::sqrt(x)); }, out);
 }
 
+namespace {
+// P(y) = sum_k c_k T_k(y) by Clenshaw.
+double cheb_sum(const double* c, int n, double y) {
+    double b1 = 0.0, b2 = 0.0;
+    for (int k = n; k >= 1; --k) {
+        const double b0 = c[k] + 2.0 * y * b1 - b2;
+        b2 = b1;
+        b1 = b0;
+    }
+    return c[0] + y * b1 - b2;
+}
+
+// Solve A z = r in place (A row-major m x m, destroyed; r becomes z); Gaussian elimination
+// with partial pivoting.  False if A is singular to working precision.
+bool lu_solve(int m, std::vector<double>& A, std::vector<double>& r) {
+    for (int k = 0; k < m; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < m; ++i)
+            if (std::fabs(A[(size_t)i * m + k]) > std::fabs(A[(size_t)piv * m + k])) piv = i;
+        if (!(std::fabs(A[(size_t)piv * m + k]) > 0.0)) return false;
+        if (piv != k) {
+            for (int j = 0; j < m; ++j) std::swap(A[(size_t)k * m + j], A[(size_t)piv * m + j]);
+            std::swap(r[k], r[piv]);
+        }
+        const double inv = 1.0 / A[(size_t)k * m + k];
+        for (int i = k + 1; i < m; ++i) {
+            const double f = A[(size_t)i * m + k] * inv;
+            if (f == 0.0) continue;
+            double* ri = &A[(size_t)i * m];
+            const double* rk = &A[(size_t)k * m];
+            for (int j = k; j < m; ++j) ri[j] -= f * rk[j];
+            r[i] -= f * r[k];
+        }
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        double s = r[k];
+        for (int j = k + 1; j < m; ++j) s -= A[(size_t)k * m + j] * r[j];
+        r[k] = s / A[(size_t)k * m + k];
+    }
+    return true;
+}
+}  // namespace
+
+double host_minimax_coeffs(int n, double eps, double* out) {
+    // Remez exchange for min over P of max over [eps, 1] of |1 - sqrt(x) P(x)|, P = sum_k c_k T_k(y),
+    // y = (2x - 1 - eps)/(1 - eps) = -cos(theta).  Reference: n + 2 angles; levelled system
+    // sqrt(x_i) P(x_i) + s_i E = 1 with alternating s_i; next reference: the alternating extrema of
+    // the error on a grid of 64 points per oscillation, each refined by a parabola in theta.
+    const double pi = std::acos(-1.0);
+    const int m = n + 2;
+    std::vector<double> th(m), sg(m), c(n + 1, 0.0);
+    for (int i = 0; i < m; ++i) {
+        th[i] = pi * i / (n + 1);
+        sg[i] = (i % 2 == 0) ? 1.0 : -1.0;
+    }
+    const int G = 64 * m;
+    const double h = pi / G;
+    auto err_at = [&](double t) {
+        const double y = -std::cos(t);
+        const double x = ((1.0 - eps) * y + 1.0 + eps) / 2.0;
+        return 1.0 - std::sqrt(x) * cheb_sum(c.data(), n, y);
+    };
+    double delta = 1.0, last_gap = 1e300;
+    std::vector<double> e(G + 1);
+    for (int it = 0; it < 80; ++it) {
+        std::vector<double> A((size_t)m * m), r(m, 1.0);
+        for (int i = 0; i < m; ++i) {
+            const double y = -std::cos(th[i]);
+            const double sx = std::sqrt(((1.0 - eps) * y + 1.0 + eps) / 2.0);
+            double t0 = 1.0, t1 = y;
+            for (int k = 0; k <= n; ++k) {
+                const double tk = (k == 0) ? 1.0 : (k == 1 ? y : 2.0 * y * t1 - t0);
+                if (k >= 2) {
+                    t0 = t1;
+                    t1 = tk;
+                }
+                A[(size_t)i * m + k] = sx * tk;
+            }
+            A[(size_t)i * m + n + 1] = sg[i];
+        }
+        if (!lu_solve(m, A, r)) break;
+        for (int k = 0; k <= n; ++k) c[k] = r[k];
+        const double E = std::fabs(r[n + 1]);
+        for (int j = 0; j <= G; ++j) e[j] = err_at(h * j);
+        // extrema (ends included), refined, then reduced to an alternating sequence
+        std::vector<double> at, av;
+        for (int j = 0; j <= G; ++j) {
+            const bool end = (j == 0 || j == G);
+            if (!end && !((e[j] - e[j - 1]) * (e[j + 1] - e[j]) <= 0.0 && e[j] != e[j - 1])) continue;
+            double t = h * j;
+            if (!end) {
+                const double den = e[j - 1] - 2.0 * e[j] + e[j + 1];
+                if (den != 0.0) t += 0.5 * h * (e[j - 1] - e[j + 1]) / den;
+            }
+            const double v = err_at(t);
+            if (!av.empty() && ((v > 0.0) == (av.back() > 0.0))) {
+                if (std::fabs(v) > std::fabs(av.back())) {
+                    at.back() = t;
+                    av.back() = v;
+                }
+            } else {
+                at.push_back(t);
+                av.push_back(v);
+            }
+        }
+        while ((int)at.size() > m) {
+            if (std::fabs(av.front()) < std::fabs(av.back())) {
+                at.erase(at.begin());
+                av.erase(av.begin());
+            } else {
+                at.pop_back();
+                av.pop_back();
+            }
+        }
+        delta = 0.0;
+        for (double v : av) delta = std::max(delta, std::fabs(v));
+        if ((int)at.size() < m) break;
+        for (int i = 0; i < m; ++i) {
+            th[i] = at[i];
+            sg[i] = av[i] > 0.0 ? 1.0 : -1.0;
+        }
+        // levelled: the gap between the largest error and E is at the rounding of the error
+        // function (~1e-14 absolute at delta ~ 1e-10), so also stop once it no longer halves
+        const double gap = (delta - E) / E;
+        if (gap <= 1e-6 || (gap < 1e-3 && gap > 0.5 * last_gap)) break;
+        last_gap = gap;
+    }
+    for (int k = 0; k <= n; ++k) out[k] = c[k];
+    return delta;
+}
+
 double host_poly_delta(const double* coeffs, int n, double eps) {
     // max |1 - sqrt(x) P(x)| on a grid uniform in the Chebyshev angle (Clenshaw in FP64)
     const int ng = 4096;

@@ -173,5 +173,8 @@ void host_chebyshev_coeffs_shifted_inverse_root(int n, double eps, double a, dou
 // delta = max over [eps, 1] of |1 - sqrt(x) P(x)| for P = sum_k coeffs[k] T_k(y) (Sec. 2, eq. 2),
 // on a grid of 4097 points uniform in the Chebyshev angle.
 double host_poly_delta(const double* coeffs, int n, double eps);
+// The degree-n polynomial of least relative error |1 - sqrt(x) P(x)| on [eps, 1] (Remez exchange),
+// in the same basis; returns its delta.
+double host_minimax_coeffs(int n, double eps, double* out);
 
 }  // namespace ovl

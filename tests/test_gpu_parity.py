@@ -169,6 +169,27 @@ def test_sign_f64_matches_oracle(P, lat4, n_ev):
     ctx.close()
 
 
+def test_sign_f64_minimax_matches_oracle(P, lat4):
+    """The minimax polynomial (poly_kind = 1): the library's Remez coefficients in the GPU
+    recurrence against the oracle's sign function with the oracle's own Remez coefficients."""
+    d = lat4
+    degree, eps = 200, EPS4
+    ctx = P.Context(P.Params(dims=d["dims"], bc=d["bc"], m0=M0, eps=eps, poly_degree=degree, poly_kind=1,
+                             max_nrhs=2))
+    ctx.set_gauge(to_dev(d["U"]))
+    P.deflate(ctx, to_dev(d["V"]), d["lam"])
+    x = synth.gaussian_spinor(d["dims"], 2, 5)
+    got = gpu_apply(P, ctx, P.apply_sign_Hw, x)
+    from oracle import chebyshev
+
+    cm, _ = chebyshev.minimax_coeffs(degree, eps)
+    p = ov.OverlapParams(m0=M0, hw_norm=d["hw"], eps=eps, degree=degree, bc=oracle_bc(d["bc"]), coeffs=cm)
+    small = ov.SmallSpace.from_eigenpairs(d["V"], d["lam"])
+    want = np.stack([ov.sign_hw(d["U"], x[j], p, small) for j in range(2)])
+    assert relerr(got, want) < F64_TOL
+    ctx.close()
+
+
 @pytest.mark.parametrize("mass", [0.0, 0.1])
 def test_overlap_f64_matches_oracle(P, lat4, mass):
     d = lat4

@@ -82,7 +82,7 @@ def test_host_eigh_degenerate(ovl):
 @pytest.mark.parametrize("bad", [dict(dims=(1, 4, 4, 4)), dict(eps=0.0), dict(eps=1.0), dict(poly_degree=0),
                                  dict(precision=7), dict(max_nrhs=0), dict(bc=(0, 0, 0, 5)),
                                  dict(inner_precision=2), dict(inner_precision=3), dict(launch_shape=3),
-                                 dict(launch_shape=32), dict(launch_shape=-1)])
+                                 dict(launch_shape=32), dict(launch_shape=-1), dict(poly_kind=2)])
 def test_create_rejects_invalid_parameters(ovl, bad):
     kw = dict(dims=(4, 4, 4, 4))
     kw.update(bad)
@@ -122,6 +122,24 @@ def test_library_polynomial_delta_matches_oracle(ovl, n, eps):
 def test_poly_delta_of_any_degree_matches_oracle(ovl, n, eps):
     want = chebyshev.approximation_error(chebyshev.chebyshev_coeffs(n, eps), eps)
     assert ovl.poly_delta(n, eps) == pytest.approx(want, rel=0.05)
+
+
+@pytest.mark.parametrize("n,eps", [(0, 0.01), (8, 0.1), (64, 0.01), (300, 4e-4)])
+def test_minimax_coefficients_match_oracle(ovl, n, eps):
+    c, d = ovl.minimax_coeffs(n, eps)
+    co, do = chebyshev.minimax_coeffs(n, eps)
+    assert d == pytest.approx(do, rel=1e-6)
+    assert np.abs(c - co).max() <= 1e-9 * np.abs(co).max()
+
+
+def test_minimax_kind_context_uses_it(ovl):
+    ctx = ovl.Context(ovl.Params(dims=(4, 4, 4, 4), eps=4e-4, poly_degree=527, poly_kind=1))
+    _, want = chebyshev.minimax_coeffs(527, 4e-4)
+    assert ctx.delta == pytest.approx(want, rel=1e-3)
+    assert ctx.delta < 1.3e-10  # eq. 2: 1e-10 at n = 527, sqrt(eps) = 0.02
+    n = ctx.adaptive_degree(1e-8)
+    assert n % 8 == 0 and chebyshev.approximation_error(chebyshev.minimax_coeffs(n, 4e-4)[0], 4e-4) <= 1e-8
+    ctx.close()
 
 
 def test_adaptive_degree_is_the_lowest_meeting_the_target(ovl):
