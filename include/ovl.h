@@ -157,6 +157,10 @@ const char* ov_tune_info(const ov_ctx* ctx);
  * last check (its output is then incomplete), OV_ERR_CUDA if the stream reports an error.
  * solve_overlap and ov_eigensolve_Q make the same check before they return. */
 int ov_sync(ov_ctx* ctx, ov_stream_t stream);
+/* Exercises the bounded-wait path on stream: one block waits about a millisecond on an mbarrier
+ * that nothing completes and records the timeout as a real wait would; the next ov_sync then
+ * returns OV_ERR_TIMEOUT and clears it.  For tests of the failure path (no fault, no hang). */
+int ov_selftest_bounded_wait(ov_ctx* ctx, ov_stream_t stream);
 /* Number of lattice sites. */
 long long ov_volume(const ov_ctx* ctx);
 /* ||H_w|| in use (after the hw_norm <= 0 default is resolved). */

@@ -44,6 +44,7 @@ from ._ovl import (  # noqa: F401
     library_path,
     pion_correlator,
     poly_delta,
+    selftest_bounded_wait,
     solve_overlap,
     sync,
     timeslice_scale,

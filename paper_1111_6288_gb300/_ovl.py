@@ -76,6 +76,7 @@ _SIGNATURES = {
     "ov_last_info": (C.c_char_p, [_VP]),
     "ov_tune_info": (C.c_char_p, [_VP]),
     "ov_sync": (_I, [_VP, _VP]),
+    "ov_selftest_bounded_wait": (_I, [_VP, _VP]),
     "ov_eigensolve_overlap": (_I, [_VP, _D, _I, _I, _I, _D, _I, _DP, _DP, _VP]),
     "ov_clear_overlap_deflation": (_I, [_VP, _D, _I]),
     "ov_volume": (C.c_longlong, [_VP]),
@@ -330,6 +331,11 @@ def eigensolve_overlap(ctx: Context, n_ev, chirality=1, phase=0.0, krylov=0, tol
 def clear_overlap_deflation(ctx: Context, phase=0.0, chirality=0):
     """Drop the D_ov deflation spaces of a phase (chirality 0: both sectors)."""
     _check(lib().ov_clear_overlap_deflation(ctx.handle, float(phase), int(chirality)), ctx.handle)
+
+
+def selftest_bounded_wait(ctx: Context, stream=None):
+    """Make one bounded device wait run out (about 1 ms); the next sync() raises OV_ERR_TIMEOUT."""
+    _check(lib().ov_selftest_bounded_wait(ctx.handle, _stream(stream)), ctx.handle)
 
 
 def sync(ctx: Context, stream=None):

@@ -976,6 +976,13 @@ const char* ov_last_info(const ov_ctx* c) { return c ? c->info.c_str() : ""; }
 
 const char* ov_tune_info(const ov_ctx* c) { return c ? c->tune_log.c_str() : ""; }
 
+int ov_selftest_bounded_wait(ov_ctx* c, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    launch_bounded_wait_selftest(2000000LL, (cudaStream_t)stream);  // about a millisecond
+    CKL();
+    return OV_OK;
+}
+
 int ov_sync(ov_ctx* c, ov_stream_t stream) {
     if (!c) return OV_ERR_ARG;
     CK(cudaStreamSynchronize((cudaStream_t)stream));

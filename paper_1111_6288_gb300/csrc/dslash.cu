@@ -491,12 +491,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for phase `parity` of bar for at most kWaitCycles; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for phase `parity` of bar for at most limit cycles; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Self-test of the bounded wait: one block waits on an mbarrier that expects bytes no copy will
+// bring, for `limit` cycles, then records the timeout exactly as the tiled kernel does.  No copy
+// is in flight, so the block returns cleanly.
+__global__ void bounded_wait_selftest_k(long long limit) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t bar_a = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar_a, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(bar_a, 16u);  // the phase now waits for 16 bytes
+    __syncthreads();
+    if (!mbar_wait_bounded(bar_a, 0, limit)) {
+        if (threadIdx.x == 0) atomicExch(&g_wait_timeouts, 1);
+    }
 }
 
 // Block = DSLASH_THREADS threads = (DSLASH_THREADS / b sites) x (b right-hand sides), b in
@@ -663,6 +681,11 @@ int tile_rows(const Geom& g, int by) {
     for (int rows = L1; rows >= 1; --rows)
         if (L1 % rows == 0 && L0 * rows * by <= DSLASH_THREADS && (L0 * rows) % 32 == 0) return rows;
     return 0;
+}
+
+void launch_bounded_wait_selftest(long long limit_cycles, cudaStream_t s) {
+    bounded_wait_selftest_k<<<1, 32, 0, s>>>(limit_cycles);
+    count_launch();
 }
 
 int take_wait_timeouts() {

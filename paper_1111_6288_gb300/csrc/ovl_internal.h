@@ -77,6 +77,8 @@ constexpr int kShapeTiled = 16;
 int tile_rows(const Geom& g, int by);
 // 1 if a bounded device wait ran out since the last call (and clears it), 0 if not, -1 on error.
 int take_wait_timeouts();
+// One block waiting on an mbarrier nothing completes, for limit_cycles: sets the timeout flag.
+void launch_bounded_wait_selftest(long long limit_cycles, cudaStream_t s);
 template <typename R>
 void launch_dslash(const Geom& g, double m0, const void* links, const void* in, void* out, int nrhs,
                    const double* d_phase, const Epilogue& e, cudaStream_t s, bool deriv = false,

@@ -62,6 +62,24 @@ def test_iteration_cap_returns_not_converged_with_the_best_iterate(P):
     ctx.close()
 
 
+def test_bounded_wait_timeout_is_reported_and_the_context_survives(P, ctx4):
+    """A device wait that runs out (an mbarrier nothing completes, ~1 ms bound) is reported by
+    the next sync as OV_ERR_TIMEOUT, once; the context keeps working afterwards."""
+    import torch
+
+    P.sync(ctx4)
+    P.selftest_bounded_wait(ctx4)
+    with pytest.raises(P.OvlError) as e:
+        P.sync(ctx4)
+    assert e.value.code == 7
+    P.sync(ctx4)  # the flag was cleared
+    x = dev(synth.gaussian_spinor(ctx4.dims, 1, 9))
+    y = torch.empty_like(x)
+    P.apply_wilson(ctx4, x, y, hermitian=True)
+    P.sync(ctx4)
+    assert torch.isfinite(y).all()
+
+
 def test_zero_right_hand_side_gives_zero(P, ctx4):
     import torch
 
