@@ -313,8 +313,11 @@ def main():
     defl_info = None
     if args.n_defl > 0:
         t1 = time.perf_counter()
-        modes = {chi: P.eigensolve_overlap(ctx_mix, args.n_defl, chirality=chi) for chi in (1, -1)}
-        defl_info = {"seconds": time.perf_counter() - t1, "n_per_sector": args.n_defl,
+        modes, lanczos = {}, []
+        for chi in (1, -1):
+            modes[chi] = P.eigensolve_overlap(ctx_mix, args.n_defl, chirality=chi)
+            lanczos.append(ctx_mix.last_info)
+        defl_info = {"seconds": time.perf_counter() - t1, "n_per_sector": args.n_defl, "lanczos": lanczos,
                      "ritz_range": [float(min(m[0][0] for m in modes.values())),
                                     float(max(m[0][-1] for m in modes.values()))],
                      "worst_residual": float(max(m[1].max() for m in modes.values()))}

@@ -292,8 +292,9 @@ int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, 
  * applied to them) is registered for (phase, chirality), replacing an earlier one; from then on
  * the FP32 inner CG of solve_overlap starts each system of that phase and chirality from the
  * Galerkin solution on it and keeps its search directions A-orthogonal to it (deflated CG), for
- * any mass (A(m) = (1 - m^2/4) A0 + m^2).  theta_out, res_out: host [n_ev] Ritz values of A0
- * (ascending) and residual norms |A0 w - theta w|, or NULL.  Synchronises stream. */
+ * any mass (A(m) = (1 - m^2/4) A0 + m^2).  The Lanczos runs at the lowest degree with
+ * delta <= tol / 10; theta_out, res_out: host [n_ev] Ritz values w^+ A0 w of the full-degree
+ * operator (FP64) and residual norms |A0 w - theta w|, or NULL.  Synchronises stream. */
 int ov_eigensolve_overlap(ov_ctx* ctx, double phase, int chirality, int n_ev, int krylov, double tol,
                           int max_restarts, double* theta_out, double* res_out, ov_stream_t stream);
 /* Drop the D_ov deflation spaces of a phase (chirality +1, -1, or 0 for both). */

@@ -1435,10 +1435,13 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
     std::vector<double> th, kept_theta;
     int kb = 0, passes = 0, steps = 0;
     double last_b = 0.0, worst_est = 0.0;
+    // the operator only needs to be a tenth of the residual target accurate: the lowest degree
+    // with delta <= tol / 10 (A0 W is recomputed in FP64 at the full degree afterwards)
+    const int ldeg = degree_for_delta(c, 0.1 * tol);
     for (;;) {
         for (int j = kb; j < K; ++j) {
             char* qj = (char*)Q + (size_t)j * vb;
-            TRY(sign_pipeline<float>(c, qj, S1, false, sector_operator(c, 0.0, qj), w, s));
+            TRY(sign_pipeline<float>(c, qj, S1, false, sector_operator(c, 0.0, qj), w, s, ldeg));
             ++steps;
             // w -= Q_{0..j} (Q^+ w), twice; the coefficients are column j of Q^+ A0 Q
             std::vector<HostCplx> gsum(j + 1, HostCplx{0, 0});
@@ -1521,7 +1524,7 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
     Sn.n = n_ev;
     Sn.phase.assign(n_ev, phase);
     Sn.chi.assign(n_ev, (signed char)chi);
-    TRY(sign_pipeline<float>(c, sp->W, Sn, false, sector_operator(c, 0.0, sp->W), sp->AW0, s));
+    TRY(sign_pipeline<float>(c, sp->W, Sn, false, sector_operator(c, 0.0, sp->W), sp->AW0, s, ldeg));
     std::vector<HostCplx> Hr, Z;
     TRY(gram_host<float>(c, sp->W, n_ev, sp->AW0, n_ev, Hr, s));
     hermitize(Hr, n_ev);
@@ -1543,9 +1546,9 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
     char buf[256];
     double worst = 0.0;
     for (double r : sp->res) worst = std::max(worst, r);
-    snprintf(buf, sizeof(buf), "D_ov low modes: phase %.6g, chirality %+d, %d Lanczos steps in %d passes of %d, %d Ritz "
-             "pairs in [%.3e, %.3e], worst residual %.2e (estimate %.2e)", phase, chi, steps, passes, K, n_ev,
-             sp->theta.front(), sp->theta.back(), worst, worst_est);
+    snprintf(buf, sizeof(buf), "D_ov low modes: phase %.6g, chirality %+d, %d Lanczos steps (degree %d) in %d passes of %d, "
+             "%d Ritz pairs in [%.3e, %.3e], worst residual %.2e (estimate %.2e)", phase, chi, steps, ldeg, passes, K,
+             n_ev, sp->theta.front(), sp->theta.back(), worst, worst_est);
     c->info = buf;
     return OV_OK;
 }
@@ -1589,6 +1592,20 @@ int dspace_fp64(ov_ctx* c, DefSpace& sp, cudaStream_t s) {
     CKL();
     sp.mass = -1.0;
     sp.Einv64.clear();
+    // Ritz values and residuals of the full-degree operator: theta_i = w_i^+ A0 w_i,
+    // |A0 w_i - theta_i w_i| (FP64)
+    std::vector<HostCplx> H;
+    TRY(gram_host<double>(c, sp.W64, sp.n, sp.AW64, sp.n, H, s));
+    std::vector<double> mth(sp.n), ones(sp.n, 1.0);
+    for (int i = 0; i < sp.n; ++i) {
+        sp.theta[i] = H[i + (size_t)i * sp.n].re;
+        mth[i] = -sp.theta[i];
+    }
+    CK(cudaMemcpyAsync(t64, sp.AW64, b64, cudaMemcpyDeviceToDevice, s));
+    launch_axpby<double>(mth.data(), sp.W64, ones.data(), t64, 12LL * c->g.V, sp.n, s);
+    CKL();
+    norm2_rhs<double>(t64, 12LL * c->g.V, sp.n, sp.res.data(), c->d_partial, c->d_red, s);
+    for (double& r : sp.res) r = std::sqrt(r);
     return OV_OK;
 }
 
