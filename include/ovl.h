@@ -110,7 +110,8 @@ typedef struct ov_params {
                              eq. 2 with A ~ 0.41, where the interpolant's is ~2x larger) */
     int adaptive_order;   /* solve_overlap: 0 = every inner sign application at poly_degree;
                              1 = per outer cycle, the lowest degree (a multiple of 8) whose
-                             interpolant has delta <= 0.5 m g, g = the cycle's inner tolerance
+                             polynomial (of poly_kind) has delta <= 0.5 m g, g = the cycle's
+                             inner tolerance
                              (the true residual keeps poly_degree; needs coeffs = NULL) */
 } ov_params;
 

@@ -6,7 +6,11 @@
 //   apply_overlap         Sec. 2, eq. 1, D_ov = 1 + gamma5 sign(H_w); D(m) = (1 - m/2) D_ov + m
 //   deflate               Sec. 2, small space from eigenvectors of Q
 //   ov_eigensolve_Q       Sec. 3.1, low eigenmodes of H_w with Chebyshev acceleration
-//   solve_overlap         Sec. 3.2, CG for D^{-1} psi, single precision late in the solve
+//   solve_overlap         Sec. 3.2, CG for D^{-1} psi, single precision late in the solve, adaptive
+//                         polynomial order, deflation with the low modes of D_ov
+//   ov_eigensolve_overlap Sec. 3.1-3.2, the D_ov low modes of one chiral sector (Lanczos)
+//   ov_create (poly_kind) Sec. 2, eq. 2, Chebyshev interpolant or minimax polynomial of x^{-1/2}
+//   ov_apply_dDdphi, ...  Sec. 4, derivatives with respect to the background field
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -85,8 +89,8 @@ struct ov_ctx {
     std::vector<double> coeffs;
     double hw_norm = 0.0;
     double delta = 0.0;  // max over [eps, 1] of |1 - sqrt(x) P(x)| (Sec. 2, eq. 2)
-    bool custom_coeffs = false;  // the caller gave the coefficients (no lower-degree interpolants)
-    // lower-degree interpolants of x^{-1/2} on the same interval and their delta, by degree
+    bool custom_coeffs = false;  // the caller gave the coefficients (no lower-degree polynomials)
+    // lower-degree polynomials of the context's kind on the same interval and their delta, by degree
     std::map<int, std::vector<double>> coeff_sets;
     std::map<int, double> delta_of;
     std::string err;
@@ -273,7 +277,7 @@ double delta_of_degree(ov_ctx* c, int n) {
     return dl;
 }
 
-// Smallest degree, a multiple of 8, whose interpolant has delta <= target (delta falls with the
+// Smallest degree, a multiple of 8, whose polynomial has delta <= target (delta falls with the
 // degree, eq. 2); poly_degree itself when no lower one does or when the coefficients are the
 // caller's.
 int degree_for_delta(ov_ctx* c, double target) {
@@ -416,8 +420,8 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
 // ST: storage of the links and vectors of the recurrence: R itself, or (R = float) a 16-bit
 // format, x_perp then being rounded to it and P(Q^2) x_perp read back into FP32 for the final
 // FP32 application of H_w.
-// degree: of the polynomial (0: the context's poly_degree; lower degrees use the interpolant of
-// that degree on the same interval).
+// degree: of the polynomial (0: the context's poly_degree; lower degrees use the polynomial of
+// that degree and the context's kind on the same interval).
 template <typename R, typename ST = R>
 int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogue fin, void* out, cudaStream_t s,
                   int degree = 0) {
