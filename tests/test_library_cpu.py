@@ -183,6 +183,29 @@ def test_calls_before_a_gauge_field_are_rejected_on_the_host(ovl):
     L.ov_destroy(h)
 
 
+def test_newer_calls_check_their_arguments_on_the_host(ovl):
+    """The D_ov eigensolver, the deflation clear, the polynomial utilities and the adaptive
+    degree reject or answer before any device work."""
+    L = ovl.lib()
+    h = _raw_ctx(ovl)
+    theta = (ctypes.c_double * 4)()
+    res = (ctypes.c_double * 4)()
+    assert L.ov_eigensolve_overlap(h, 0.0, 1, 4, 0, 1e-4, 5, theta, res, None) == 9  # no gauge yet
+    assert L.ov_clear_overlap_deflation(h, 0.0, 0) == 0  # nothing registered: nothing to free
+    assert L.ov_clear_overlap_deflation(None, 0.0, 0) == 1
+    assert L.ov_eigensolve_overlap(None, 0.0, 1, 4, 0, 1e-4, 5, theta, res, None) == 1
+    L.ov_destroy(h)
+    out = (ctypes.c_double * 8)()
+    assert L.ov_minimax_coeffs(-1, 0.01, out) < 0
+    assert L.ov_minimax_coeffs(4, 1.5, out) < 0
+    assert L.ov_minimax_coeffs(4, 0.01, None) < 0
+    assert L.ov_poly_delta_n(0, 0.01) < 0
+    assert L.ov_poly_delta_n(10, 0.0) < 0
+    assert L.ov_adaptive_degree(None, 1e-6) == 0
+    assert L.ov_selftest_bounded_wait(None, None) == 1
+    assert L.ov_sync(None, None) == 1
+
+
 def test_error_codes_for_invalid_arguments(ovl):
     L = ovl.lib()
     h = _raw_ctx(ovl)
