@@ -279,6 +279,28 @@ int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_ite
 int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, void* x,
                   int nrhs, double tol, ov_solve_stats* stats, ov_stream_t stream);
 
+/* Most masses one solve_overlap_multimass call takes. */
+#define OV_MAX_MASSES 32
+
+/* Solve D(m_i) x_i = b for n_mass masses at once (Sec. 3.2, the multi-mass CG), each to
+ * ||b - D(m_i) x_i|| / ||b|| <= tol.  The chiral-sector operators of all masses are shifts of
+ * one operator, P_s [2(1 - m^2/4)(1 + s sign) + m^2] P_s = (1 - m^2/4)(A0 + m^2/(1 - m^2/4)),
+ * A0 = P_s 2 (1 + s sign) P_s; so the first defect-correction cycle, whose residual is b for
+ * every mass, runs one multi-shift CG (one sign application per iteration and sector for all
+ * masses, the lightest mass's Krylov space, no D_ov deflation) in ctx inner_precision, and
+ * x_i = D(m_i)^+ y_i.  Each mass then continues as solve_overlap from x_i (FP64 true residual,
+ * deflated inner cycles).  masses: host [n_mass], 1 <= n_mass <= OV_MAX_MASSES, each finite with
+ * |m| < 2.  b: device [nrhs][site][4][3] complex128; x: device [n_mass][nrhs][site][4][3]
+ * complex128, output only (its contents on input are ignored); b and x must not overlap.
+ * phase: host [nrhs] (NULL = all zero).  stats: host [n_mass] or NULL; stats[i] covers mass
+ * i's own cycles plus the shared cycle's count in outer_iters and inner_iters, and the shared
+ * cycle's sign applications, Wilson applications and time are added to stats[0] only, so that
+ * sums over the masses give the call's totals.  Returns the first error other than
+ * OV_ERR_NOT_CONVERGED, else OV_ERR_NOT_CONVERGED if any mass missed tol, else OV_OK. */
+int solve_overlap_multimass(ov_ctx* ctx, int n_mass, const double* masses, const double* phase,
+                            const void* b, void* x, int nrhs, double tol, ov_solve_stats* stats,
+                            ov_stream_t stream);
+
 /* Low modes of D_ov for the CG deflation of solve_overlap (Sec. 3.2: the paper deflates its CG
  * with the D_ov eigensystem).  Computes the n_ev lowest eigenpairs of the chiral-sector operator
  * A0 = P_s [2 (1 + s sign(H_w))] P_s = P_s D_ov^+ D_ov P_s, s = chirality (+1 or -1), at the field

@@ -46,6 +46,7 @@ from ._ovl import (  # noqa: F401
     poly_delta,
     selftest_bounded_wait,
     solve_overlap,
+    solve_overlap_multimass,
     sync,
     timeslice_scale,
 )

@@ -98,6 +98,7 @@ _SIGNATURES = {
     "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
     "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
     "solve_overlap": (_I, [_VP, _D, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),
+    "solve_overlap_multimass": (_I, [_VP, _I, _DP, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),
     "ov_apply_dHdphi": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
     "ov_apply_dDdphi": (_I, [_VP, _VP, _VP, _I, _D, _DP, _VP]),
     "ov_correlator": (_I, [_VP, _VP, _I, _DP, _VP]),
@@ -409,6 +410,33 @@ def solve_overlap(ctx: Context, b, x, mass, tol=1e-10, phase=None, stream=None, 
                              float(tol), C.byref(st), _stream(stream))
     stats = SolveStats(st.status, st.outer_iters, st.inner_iters, st.sign_applies, st.dslash_calls, st.true_residual,
                        st.seconds)
+    if raise_on_error:
+        _check(rc, ctx.handle)
+    return stats
+
+
+def solve_overlap_multimass(ctx: Context, b, x, masses, tol=1e-10, phase=None, stream=None, raise_on_error=True):
+    """Solve D(m_i) x[i] = b for every mass (the multi-mass CG: one shared first cycle, then each
+    mass on its own).  b: [nrhs, ...sites, 4, 3] complex128; x: [n_mass, nrhs, ...] complex128,
+    output only.  Returns one SolveStats per mass (the shared cycle's work in the first)."""
+    import torch
+
+    masses = [float(m) for m in masses]
+    nm = len(masses)
+    if nm < 1:
+        raise ValueError("at least one mass")
+    n = ctx._check_spinor(b, "b", dtype=torch.complex128)
+    if not isinstance(x, torch.Tensor) or x.dim() < 2 or x.shape[0] != nm:
+        raise ValueError(f"x must have shape (n_mass = {nm}, nrhs, ...)")
+    if ctx._check_spinor(x[0], "x[0]", dtype=torch.complex128) != n or not x.is_contiguous():
+        raise ValueError("x[i] must match b's shape and x must be contiguous")
+    keep, ph = _phase_ptr(phase, n)
+    marr = np.ascontiguousarray(masses, dtype=np.float64)
+    st = (_SolveStats * max(nm, 1))()
+    rc = lib().solve_overlap_multimass(ctx.handle, nm, marr.ctypes.data_as(_DP), ph, C.c_void_p(b.data_ptr()),
+                                       C.c_void_p(x.data_ptr()), n, float(tol), st, _stream(stream))
+    stats = [SolveStats(s.status, s.outer_iters, s.inner_iters, s.sign_applies, s.dslash_calls, s.true_residual,
+                        s.seconds) for s in st[:nm]]
     if raise_on_error:
         _check(rc, ctx.handle)
     return stats

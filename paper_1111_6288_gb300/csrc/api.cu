@@ -1766,6 +1766,189 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
     return na > 0 ? OV_ERR_NOT_CONVERGED : OV_OK;
 }
 
+// Multi-shift CG: the multi-mass CG of Sec. 3.2.  The chiral-sector operators of all masses form
+// one shifted family, A(m) = k(m) (A0 + sigma(m)) with A0 = P_s 2 (1 + s sign) P_s, k(m) = 1 - m^2/4
+// and sigma(m) = m^2 / k(m).  With M = A(m_b) of the lightest mass,
+// A(m_i) = (k_i / k_b) (M + tau_i), tau_i = k_b (sigma_i - sigma_b) >= 0, so one Krylov space of M
+// serves every mass: each shifted residual stays parallel to the seed's, r_i = zeta_i r, and
+// zeta_i, alpha_i and beta_i follow from the seed's alpha and beta by scalar recurrences
+// (Jegerlehner, hep-lat/9612014).  One sign application per iteration and system, whatever the
+// number of masses.  Z is [mass][system]; Z[i][k] returns A(m_i)^{-1} B_k (the factor k_b / k_i
+// applied).  A shift whose residual |zeta_i| |r| meets its system's tolerance stops updating; a
+// system leaves the batch when its seed (the lightest mass, the last to converge) does.
+template <typename R>
+int inner_cg_shifted(ov_ctx* c, const std::vector<double>& mass, const SysSet& S0, const void* B, void* Z,
+                     const std::vector<double>& tol_rel0, int max_iter, int* iters, cudaStream_t s, int degree) {
+    const int prec = prec_of<R>();
+    const int ns = S0.n, nm = (int)mass.size();
+    const long long n12 = 12LL * c->g.V;
+    const size_t vb = vec_bytes(c, prec);
+    const size_t bytes = vb * ns;
+    int ib = 0;
+    for (int i = 1; i < nm; ++i)
+        if (std::fabs(mass[i]) < std::fabs(mass[ib])) ib = i;
+    const double mb2 = mass[ib] * mass[ib];
+    const double kb = 1.0 - 0.25 * mb2;
+    std::vector<double> tau(nm);
+    for (int i = 0; i < nm; ++i) {
+        const double m2 = mass[i] * mass[i];
+        tau[i] = kb * (m2 / (1.0 - 0.25 * m2) - mb2 / kb);
+    }
+    void *r, *Ap, *tmp, *P;
+    TRY(workspace(c, "mcg_r", prec, ns, &r));
+    TRY(workspace(c, "mcg_Ap", prec, ns, &Ap));
+    TRY(workspace(c, "mcg_tmp", prec, 1, &tmp));
+    TRY(workspace(c, "mcg_p", prec, (long long)nm * ns, &P));
+    auto at = [&](void* base, int i, int k) { return (char*)base + ((size_t)i * ns + k) * vb; };
+    CK(cudaMemcpyAsync(r, B, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < nm; ++i) {
+        CK(cudaMemcpyAsync(at(P, i, 0), B, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(at(Z, i, 0), 0, bytes, s));
+    }
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * ns, ns));
+    SysSet S = S0;
+    std::vector<double> tol_rel = tol_rel0;
+    std::vector<int> perm(ns);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::vector<double> rr(ns), rr_new(ns), b2(ns), alpha(ns), beta(ns), ones(ns, 1.0);
+    std::vector<double> a_prev(ns, 1.0), b_prev(ns, 0.0), ca(ns), cb(ns);
+    // per (mass, system), index i * ns + k: zeta_k, zeta_{k-1}, zeta_{k+1}; frozen once converged
+    std::vector<double> z((size_t)nm * ns, 1.0), zp((size_t)nm * ns, 1.0), zn((size_t)nm * ns, 1.0);
+    std::vector<char> frozen((size_t)nm * ns, 0);
+    std::vector<double2> pap(ns);
+    norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
+    b2 = rr;
+    auto swap_vec = [&](char* bi, char* bj) -> int {
+        CK(cudaMemcpyAsync(tmp, bi, vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bi, bj, vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bj, tmp, vb, cudaMemcpyDeviceToDevice, s));
+        return OV_OK;
+    };
+    // drop position k from the active front [0, na)
+    auto retire = [&](int k, int& na) -> int {
+        const int last = na - 1;
+        if (k != last) {
+            TRY(swap_vec((char*)r + (size_t)k * vb, (char*)r + (size_t)last * vb));
+            for (int i = 0; i < nm; ++i) {
+                TRY(swap_vec(at(P, i, k), at(P, i, last)));
+                TRY(swap_vec(at(Z, i, k), at(Z, i, last)));
+                const size_t q = (size_t)i * ns + k, ql = (size_t)i * ns + last;
+                std::swap(z[q], z[ql]);
+                std::swap(zp[q], zp[ql]);
+                std::swap(frozen[q], frozen[ql]);
+            }
+            std::swap(perm[k], perm[last]);
+            std::swap(rr[k], rr[last]);
+            std::swap(b2[k], b2[last]);
+            std::swap(tol_rel[k], tol_rel[last]);
+            std::swap(a_prev[k], a_prev[last]);
+            std::swap(b_prev[k], b_prev[last]);
+            std::swap(S.phase[k], S.phase[last]);
+            std::swap(S.chi[k], S.chi[last]);
+        }
+        --na;
+        return OV_OK;
+    };
+    int na = ns;
+    for (int k = na - 1; k >= 0; --k)
+        if (!(rr[k] > 0.0)) TRY(retire(k, na));
+    const double k1 = 2.0 * kb;
+    Epilogue fin;
+    fin.c_op = k1 / c->hw_norm;
+    fin.c1 = k1;
+    fin.chi = c->d_chi;
+    fin.c2 = k1 + mb2;
+    int it = 0;
+    for (it = 0; it < max_iter && na > 0; ++it) {
+        SysSet A;
+        A.n = na;
+        A.phase.assign(S.phase.begin(), S.phase.begin() + na);
+        A.chi.assign(S.chi.begin(), S.chi.begin() + na);
+        void* pb = at(P, ib, 0);
+        fin.v2 = pb;
+        TRY(sign_pipeline<R>(c, pb, A, false, fin, Ap, s, degree));  // Ap = M p (seed direction)
+        dot_rhs<R>(pb, Ap, n12, na, pap.data(), c->d_partial, c->d_red, s);
+        for (int k = 0; k < na; ++k) {
+            if (!std::isfinite(pap[k].x) || !std::isfinite(rr[k]))
+                return fail(c, OV_ERR_NAN, "multi-mass CG: NaN/Inf in <p, M p> (system %d, iteration %d)", perm[k], it);
+            if (pap[k].x <= 0.0)
+                return fail(c, OV_ERR_BREAKDOWN, "multi-mass CG: <p, M p> = %g <= 0 (system %d, iteration %d)",
+                            pap[k].x, perm[k], it);
+            alpha[k] = rr[k] / pap[k].x;
+        }
+        // zeta_{k+1} = zeta_k zeta_{k-1} a_{k-1} / (a_k b_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} a_{k-1} (1 + tau a_k));
+        // x_i += (a_k zeta_{k+1} / zeta_k) p_i
+        for (int i = 0; i < nm; ++i) {
+            for (int k = 0; k < na; ++k) {
+                const size_t q = (size_t)i * ns + k;
+                ca[k] = 0.0;
+                if (frozen[q]) continue;
+                const double den = alpha[k] * b_prev[k] * (zp[q] - z[q]) + zp[q] * a_prev[k] * (1.0 + tau[i] * alpha[k]);
+                zn[q] = z[q] * zp[q] * a_prev[k] / den;
+                if (!std::isfinite(zn[q]) || zn[q] == 0.0)
+                    return fail(c, OV_ERR_BREAKDOWN, "multi-mass CG: shift recurrence broke down (mass %d, system %d)",
+                                i, perm[k]);
+                ca[k] = alpha[k] * zn[q] / z[q];
+            }
+            launch_axpby<R>(ca.data(), at(P, i, 0), ones.data(), at(Z, i, 0), n12, na, s);
+        }
+        for (int k = 0; k < na; ++k) ca[k] = -alpha[k];
+        launch_axpby<R>(ca.data(), Ap, ones.data(), r, n12, na, s);  // r -= alpha M p
+        CKL();
+        norm2_rhs<R>(r, n12, na, rr_new.data(), c->d_partial, c->d_red, s);
+        for (int k = 0; k < na; ++k) beta[k] = rr_new[k] / rr[k];
+        // p_i = zeta_{k+1} r + beta (zeta_{k+1} / zeta_k)^2 p_i
+        for (int i = 0; i < nm; ++i) {
+            for (int k = 0; k < na; ++k) {
+                const size_t q = (size_t)i * ns + k;
+                if (frozen[q]) {
+                    ca[k] = 0.0;
+                    cb[k] = 1.0;
+                    continue;
+                }
+                const double t = zn[q] / z[q];
+                ca[k] = zn[q];
+                cb[k] = beta[k] * t * t;
+            }
+            launch_axpby<R>(ca.data(), r, cb.data(), at(P, i, 0), n12, na, s);
+        }
+        CKL();
+        for (int k = 0; k < na; ++k) {
+            for (int i = 0; i < nm; ++i) {
+                const size_t q = (size_t)i * ns + k;
+                if (frozen[q]) continue;
+                zp[q] = z[q];
+                z[q] = zn[q];
+            }
+            a_prev[k] = alpha[k];
+            b_prev[k] = beta[k];
+            rr[k] = rr_new[k];
+            for (int i = 0; i < nm; ++i) {
+                const size_t q = (size_t)i * ns + k;
+                if (!frozen[q] && std::fabs(z[q]) * std::sqrt(rr[k]) <= tol_rel[k] * std::sqrt(b2[k])) frozen[q] = 1;
+            }
+        }
+        for (int k = na - 1; k >= 0; --k)
+            if (frozen[(size_t)ib * ns + k]) TRY(retire(k, na));
+    }
+    *iters = it;
+    // back to the original order (position k holds system perm[k]) and A(m_i)^-1 = (k_b / k_i) (M + tau_i)^-1
+    bool moved = false;
+    for (int k = 0; k < ns; ++k) moved = moved || perm[k] != k;
+    void* Zo = nullptr;
+    if (moved) TRY(workspace(c, "mcg_zorder", prec, ns, &Zo));
+    for (int i = 0; i < nm; ++i) {
+        if (moved) {
+            for (int k = 0; k < ns; ++k)
+                CK(cudaMemcpyAsync((char*)Zo + (size_t)perm[k] * vb, at(Z, i, k), vb, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(at(Z, i, 0), Zo, bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        launch_scale<R>(kb / (1.0 - 0.25 * mass[i] * mass[i]), at(Z, i, 0), at(Z, i, 0), n12 * ns, s);
+    }
+    CKL();
+    return na > 0 ? OV_ERR_NOT_CONVERGED : OV_OK;
+}
+
 template <typename R>
 int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* x, double tol, ov_solve_stats* st,
                cudaStream_t s) {
@@ -1990,7 +2173,159 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
     return OV_OK;
 }
 
+// Several masses from one right-hand side set (the multi-mass CG of Sec. 3.2).  The first
+// defect-correction cycle is shared: its residual is b for every mass (x0 = 0), so one
+// multi-shift CG over the chiral sectors of b (undeflated: a shared Krylov space cannot carry a
+// per-mass deflation) gives y_i for all masses, and x_i = D(m_i)^+ y_i.  Each mass then finishes
+// in solve_impl from x_i (FP64 true residual, deflated cycles).  x: [mass][rhs] ABI spinors.
+template <typename R>
+int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& Srhs, const void* b, void* x,
+                     double tol, ov_solve_stats* st, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nrhs = Srhs.n, nm = (int)mass.size(), V = c->g.V;
+    const long long n12 = 12LL * V;
+    const int prec = prec_of<R>();
+    const size_t vb64 = vec_bytes(c, OV_PREC_F64), vb = vec_bytes(c, prec);
+    const size_t abi_bytes = (size_t)nrhs * (size_t)n12 * 16;  // complex128 ABI spinors of one mass
+    void *B, *S64, *Bs, *Z, *Ysum, *E, *E64;
+    TRY(workspace(c, "mm_B", OV_PREC_F64, nrhs, &B));
+    TRY(workspace(c, "mm_S64", OV_PREC_F64, 2 * nrhs, &S64));
+    TRY(workspace(c, "mm_Bs", prec, 2 * nrhs, &Bs));
+    TRY(workspace(c, "mm_Z", prec, (long long)nm * 2 * nrhs, &Z));
+    TRY(workspace(c, "mm_Ysum", prec, nrhs, &Ysum));
+    TRY(workspace(c, "mm_E", prec, nrhs, &E));
+    TRY(workspace(c, "mm_E64", OV_PREC_F64, nrhs, &E64));
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * 2 * nrhs, 2 * nrhs));
+    launch_pack_spinor<double>(b, OV_C128, B, V, nrhs, s);
+    CKL();
+    const long long dslash0 = c->dslash_count, sign0 = c->sign_count;
+    std::vector<double> bn2(nrhs);
+    norm2_rhs<double>(B, n12, nrhs, bn2.data(), c->d_partial, c->d_red, s);
+    for (int j = 0; j < nrhs; ++j)
+        if (!std::isfinite(bn2[j])) return fail(c, OV_ERR_NAN, "NaN/Inf in b (rhs %d)", j);
+    // chiral sectors of b
+    std::vector<int> src, sys_of_rhs(2 * nrhs, -1);
+    std::vector<signed char> chi;
+    for (int j = 0; j < nrhs; ++j)
+        if (bn2[j] > 0.0)
+            for (int sg = 0; sg < 2; ++sg) {
+                src.push_back(j);
+                chi.push_back(sg == 0 ? 1 : -1);
+            }
+    const int ns0 = (int)src.size();
+    SysSet S;
+    std::vector<double> tol_rel;
+    int ns = 0, iters = 0, degree = 0, rc = OV_OK;
+    if (ns0 > 0) {
+        CK(cudaMemcpyAsync(c->d_idx, src.data(), sizeof(int) * ns0, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->d_chi, chi.data(), ns0, cudaMemcpyHostToDevice, s));
+        launch_chiral_split<double>(B, S64, c->d_idx, c->d_chi, V, ns0, s);
+        CKL();
+        std::vector<double> sn2(ns0);
+        norm2_rhs<double>(S64, n12, ns0, sn2.data(), c->d_partial, c->d_red, s);
+        const double base_tol = c->p.inner_tol > 0.0 ? c->p.inner_tol : (prec == OV_PREC_F64 ? 0.0 : 1e-6);
+        for (int k = 0; k < ns0; ++k) {
+            const int j = src[k];
+            if (!(sn2[k] > 0.0) || std::sqrt(sn2[k]) <= 0.25 * tol * std::sqrt(bn2[j])) continue;
+            if (ns != k)
+                CK(cudaMemcpyAsync((char*)S64 + (size_t)ns * vb64, (char*)S64 + (size_t)k * vb64, vb64,
+                                   cudaMemcpyDeviceToDevice, s));
+            S.phase.push_back(Srhs.phase[j]);
+            S.chi.push_back(chi[k]);
+            sys_of_rhs[2 * j + (chi[k] > 0 ? 0 : 1)] = ns;
+            tol_rel.push_back(std::min(0.5, std::max(base_tol, 0.5 * tol * std::sqrt(bn2[j] / sn2[k]))));
+            ++ns;
+        }
+        S.n = ns;
+    }
+    if (ns > 0) {
+        if (std::is_same<R, double>::value)
+            CK(cudaMemcpyAsync(Bs, S64, vb64 * ns, cudaMemcpyDeviceToDevice, s));
+        else
+            launch_convert<double, float>(S64, Bs, V, ns, s);
+        CKL();
+        // adaptive order: the rule of solve_impl with the lightest mass, which binds
+        if (c->p.adaptive_order) {
+            double g = 1.0, mmin = std::fabs(mass[0]);
+            for (double t : tol_rel) g = std::min(g, t);
+            for (double m : mass) mmin = std::min(mmin, std::fabs(m));
+            degree = degree_for_delta(c, 0.5 * mmin * g);
+        }
+        rc = inner_cg_shifted<R>(c, mass, S, Bs, Z, tol_rel, c->p.max_iter, &iters, s, degree);
+        if (rc != OV_OK && rc != OV_ERR_NOT_CONVERGED) return rc;
+    }
+    // x_i = D(m_i)^+ (y_{i,+} + y_{i,-})
+    for (int i = 0; i < nm; ++i) {
+        char* xi = (char*)x + (size_t)i * abi_bytes;
+        if (ns == 0) {
+            CK(cudaMemsetAsync(xi, 0, abi_bytes, s));
+            continue;
+        }
+        CK(cudaMemcpyAsync(c->d_idx, sys_of_rhs.data(), sizeof(int) * 2 * nrhs, cudaMemcpyHostToDevice, s));
+        dim3 grid(std::min<long long>((n12 + 255) / 256, 152 * 4), nrhs);
+        merge_sectors_k<R><<<grid, 256, 0, s>>>((const typename C2<R>::T*)((char*)Z + (size_t)i * ns * vb), c->d_idx,
+                                                (typename C2<R>::T*)Ysum, n12);
+        count_launch();
+        CKL();
+        TRY(overlap_op<R>(c, Ysum, Srhs, mass[i], true, E, s, degree));
+        if (std::is_same<R, double>::value)
+            CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        else
+            launch_convert<float, double>(E, E64, V, nrhs, s);
+        launch_unpack_spinor<double>(E64, xi, OV_C128, V, nrhs, s);
+        CKL();
+    }
+    CK(cudaStreamSynchronize(s));
+    const long long shared_sign = c->sign_count - sign0, shared_dslash = c->dslash_count - dslash0;
+    const double shared_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    char buf[160];
+    snprintf(buf, sizeof(buf), "multi-mass: %d masses, shared cycle n %d, %d inner, %d systems%s", nm,
+             degree > 0 ? degree : c->p.poly_degree, iters, ns, rc == OV_OK ? "" : " (not converged)");
+    std::string info = buf;
+    int status = OV_OK;
+    for (int i = 0; i < nm; ++i) {
+        ov_solve_stats sti{};
+        const int rci = solve_impl<R>(c, mass[i], Srhs, b, (char*)x + (size_t)i * abi_bytes, tol, &sti, s);
+        snprintf(buf, sizeof(buf), " || m %g: ", mass[i]);
+        info += buf + c->info;
+        if (st) {
+            st[i] = sti;
+            st[i].outer_iters += ns > 0 ? 1 : 0;
+            st[i].inner_iters += iters;
+            if (i == 0) {
+                st[i].sign_applies += shared_sign;
+                st[i].dslash_calls += shared_dslash;
+                st[i].seconds += shared_s;
+            }
+        }
+        if (rci != OV_OK) {
+            if (rci != OV_ERR_NOT_CONVERGED) return rci;
+            status = rci;
+        }
+    }
+    c->info = info;
+    return status;
+}
+
 }  // namespace
+
+extern "C" int solve_overlap_multimass(ov_ctx* c, int n_mass, const double* masses, const double* phase, const void* b,
+                                       void* x, int nrhs, double tol, ov_solve_stats* stats, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    if (n_mass < 1 || n_mass > OV_MAX_MASSES || !masses)
+        return fail(c, OV_ERR_ARG, "n_mass = %d outside [1, %d] or no masses", n_mass, OV_MAX_MASSES);
+    std::vector<double> m(masses, masses + n_mass);
+    for (double v : m)
+        if (!std::isfinite(v) || !(std::fabs(v) < 2.0))
+            return fail(c, OV_ERR_ARG, "mass %g: each mass must be finite with |m| < 2", v);
+    if (!(tol > 0.0)) return fail(c, OV_ERR_ARG, "tol must be > 0");
+    TRY(check_ready(c, b, x, nrhs));
+    SysSet S = make_sys(nrhs, phase);
+    TRY(phase_check(c, S));
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->p.inner_precision == OV_PREC_F64 ? solve_multi_impl<double>(c, m, S, b, x, tol, stats, s)
+                                               : solve_multi_impl<float>(c, m, S, b, x, tol, stats, s);
+}
 
 extern "C" int solve_overlap(ov_ctx* c, double mass, const double* phase, const void* b, void* x, int nrhs, double tol,
                              ov_solve_stats* stats, ov_stream_t stream) {

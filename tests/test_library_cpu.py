@@ -206,6 +206,33 @@ def test_newer_calls_check_their_arguments_on_the_host(ovl):
     assert L.ov_sync(None, None) == 1
 
 
+def test_multimass_solve_checks_its_arguments_on_the_host(ovl):
+    """solve_overlap_multimass: the mass list and tolerance are checked before the state check,
+    and no device work starts on a rejected call."""
+    L = ovl.lib()
+    h = _raw_ctx(ovl)
+    a, b = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000)
+    st = (ovl._ovl._SolveStats * 4)()
+
+    def call(masses, n=None, tol=1e-10, ctx=h):
+        arr = (ctypes.c_double * max(len(masses), 1))(*masses)
+        return L.solve_overlap_multimass(ctx, len(masses) if n is None else n, arr, None, a, b, 1, tol, st, None)
+
+    assert call([0.1], ctx=None) == 1
+    assert call([], n=0) == 1
+    assert b"n_mass" in L.ov_last_error(h)
+    assert call([0.1] * 33) == 1  # more than OV_MAX_MASSES
+    assert call([0.1, float("nan")]) == 1
+    assert call([0.1, 2.0]) == 1  # |m| < 2: the shift m^2 / (1 - m^2/4) must be finite
+    assert call([0.1, -2.5]) == 1
+    assert call([0.1, 0.2], tol=0.0) == 1
+    assert call([0.1, 0.2]) == 9  # valid masses: the missing gauge field is reported
+    assert b"gauge" in L.ov_last_error(h)
+    arr = (ctypes.c_double * 2)(0.1, 0.2)
+    assert L.solve_overlap_multimass(h, 2, arr, None, a, a, 1, 1e-10, st, None) == 9  # state first
+    L.ov_destroy(h)
+
+
 def test_error_codes_for_invalid_arguments(ovl):
     L = ovl.lib()
     h = _raw_ctx(ovl)
