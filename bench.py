@@ -247,6 +247,66 @@ def kernel_case(dims, precision="f32", shape=0):
     ctx.close()
 
 
+MULTI_MASSES = (0.02, 0.03, 0.045, 0.06, 0.08, 0.1, 0.15)  # a ladder of seven masses (Sec. 4 uses seven)
+
+
+def multimass_case(n_defl):
+    """Seven masses from one point source on the solve's workload (16^3x32, 50 H_w modes,
+    n_defl D_ov low modes per sector, adaptive order, minimax polynomial): the multi-mass solve
+    against single-mass solves of the same masses, all to 1e-10 true residual.  Prints one JSON
+    object (a case study, not the bench line)."""
+    import torch
+
+    import paper_1111_6288_gb300 as P
+    import synth
+
+    torch.cuda.set_device(0)
+    U = torch.from_numpy(synth.random_su3_field(DIMS, LINK_EPS, 0)).cuda()
+    ctx = P.Context(P.Params(dims=DIMS, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE, max_nrhs=2, poly_kind=1,
+                             precision=P.OV_PREC_F32, inner_precision=P.OV_PREC_F32, adaptive_order=1))
+    ctx.set_gauge(U)
+    del U
+    t0 = time.perf_counter()
+    P.eigensolve_Q(ctx, N_EV, tol=1e-10, max_iter=200, register=True)
+    for chi in (1, -1) if n_defl > 0 else ():
+        P.eigensolve_overlap(ctx, n_defl, chirality=chi)
+    setup_s = time.perf_counter() - t0
+    print(f"multimass_case: setup {setup_s:.1f} s", flush=True)
+    b = torch.from_numpy(synth.point_sources(DIMS, [(0, 0)])).cuda()
+    x = torch.zeros_like(b)
+    P.solve_overlap(ctx, b, x, MULTI_MASSES[0], tol=TOL)  # graphs, launch shapes
+    torch.cuda.synchronize()
+    X = torch.empty((len(MULTI_MASSES),) + tuple(b.shape), dtype=b.dtype, device=b.device)
+    t0 = time.perf_counter()
+    sts = P.solve_overlap_multimass(ctx, b, X, MULTI_MASSES, tol=TOL)
+    torch.cuda.synchronize()
+    t_multi = time.perf_counter() - t0
+    info = ctx.last_info
+    print(f"multimass_case: multi-mass {t_multi:.2f} s: {info}", flush=True)
+    t_single, single, diff = 0.0, [], 0.0
+    for i, m in enumerate(MULTI_MASSES):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = P.solve_overlap(ctx, b, x, m, tol=TOL)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t0
+        single.append(st)
+        diff = max(diff, float((X[i] - x).norm() / x.norm()))
+    out = {"multimass_case": {
+        "workload": WORKLOAD, "masses": list(MULTI_MASSES), "n_defl_per_sector": n_defl, "setup_s": setup_s,
+        "multi_s": t_multi, "single_s": t_single, "speedup": t_single / t_multi,
+        "multi_sign_applies": sum(s.sign_applies for s in sts),
+        "single_sign_applies": sum(s.sign_applies for s in single),
+        "multi_wilson_applies": sum(s.dslash_calls for s in sts),
+        "single_wilson_applies": sum(s.dslash_calls for s in single),
+        "worst_true_residual": max(s.true_residual for s in sts + single),
+        "max_rel_diff_multi_vs_single": diff, "multi_info": info,
+        "single_inner_iters": [s.inner_iters for s in single]}}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,12 +326,18 @@ def main():
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"], help="precision of the profiling case")
     ap.add_argument("--kernel-shape", type=int, default=0,
                     help="launch shape of the profiling case (ov_params.launch_shape; 0 = timed by the library)")
+    ap.add_argument("--multimass-case", action="store_true",
+                    help="case study: seven masses by the multi-mass solve against single-mass solves, "
+                         "then exit without a bench line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.multimass_case:
+        multimass_case(args.n_defl)
         return
     if args.kernel_case:
         kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision, args.kernel_shape)
