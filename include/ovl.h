@@ -10,6 +10,7 @@
  *                   exact on the small space spanned by low eigenvectors of Q;
  *   Sec. 2, eq. 2   delta = |1 - sqrt(x) P(x)| ~ A exp(-b n sqrt(eps));
  *   Sec. 3.2        CG for D^{-1} psi, single precision late in the solve;
+ *                   multi-mass CG: several quark masses from one Krylov space;
  *   Sec. 4          background field: U_mu -> exp(-i q A_mu) U_mu, Dirichlet
  *                   boundaries in the field direction and in time.
  *
@@ -35,8 +36,9 @@
  *
  * Streams: every call takes a cudaStream_t (0 = legacy default stream) and
  * enqueues its work on it.  apply_* and deflate return once the work is
- * enqueued; solve_overlap, ov_eigensolve_Q and ov_estimate_hw_norm read
- * scalars back and so synchronise the stream.  A context is not thread-safe.
+ * enqueued; solve_overlap, solve_overlap_multimass, ov_eigensolve_Q and
+ * ov_estimate_hw_norm read scalars back and so synchronise the stream.  A
+ * context is not thread-safe.
  *
  * Errors: every int-returning call returns OV_OK or one of OV_ERR_*;
  * ov_last_error(ctx) gives a message for the last failure on that context.

@@ -8,6 +8,8 @@
 //   ov_eigensolve_Q       Sec. 3.1, low eigenmodes of H_w with Chebyshev acceleration
 //   solve_overlap         Sec. 3.2, CG for D^{-1} psi, single precision late in the solve, adaptive
 //                         polynomial order, deflation with the low modes of D_ov
+//   solve_overlap_multimass  Sec. 3.2, multi-mass CG: a multi-shift CG cycle shared by the masses,
+//                         then the cycles of solve_overlap per mass
 //   ov_eigensolve_overlap Sec. 3.1-3.2, the D_ov low modes of one chiral sector (Lanczos)
 //   ov_create (poly_kind) Sec. 2, eq. 2, Chebyshev interpolant or minimax polynomial of x^{-1/2}
 //   ov_apply_dDdphi, ...  Sec. 4, derivatives with respect to the background field
