@@ -399,6 +399,36 @@ def test_massive_overlap_normalisation(setup_2x4):
     assert np.linalg.norm(ov.overlap(U, x, 2.0, params, small) - 2.0 * x) < 1e-14
 
 
+@pytest.mark.parametrize("mass", [0.02, 0.3, -0.1, 1.5])
+def test_massive_normal_operator_is_a_shifted_family(setup_2x4, mass):
+    """With sign^2 = 1 and sign Hermitian, D(m) D(m)^+ = (1 - m^2/4) D_ov D_ov^+ + m^2, and on a
+    chiral sector P_s D(m) D(m)^+ P_s = k (A0 + (m^2 / k) P_s), A0 = 2 P_s (1 + s sign) P_s,
+    k = 1 - m^2/4: one operator shifted by a constant per mass, the form that the chiral-sector
+    CG and the multi-mass CG solve.  Exact with the exact sign; within a few delta with the
+    oracle's polynomial D(m) and D(m)^+."""
+    U, params, small, lam_q, W_all, _ = setup_2x4
+    n = W_all.shape[0]
+    G5 = np.kron(np.eye(n // 12), np.kron(dirac.GAMMA5, np.eye(3)))
+    S = dense.exact_sign_matrix(lam_q, W_all)
+    I = np.eye(n)
+    Dov = I + G5 @ S
+    Dm = (1 - mass / 2) * Dov + mass * I
+    k = 1 - mass * mass / 4
+    assert np.abs(Dm @ Dm.conj().T - (k * Dov @ Dov.conj().T + mass * mass * I)).max() < 1e-12
+    x = synth.gaussian_spinor((2, 2, 2, 2), 1, 61)[0]
+    delta = chebyshev.approximation_error(params.coeffs, params.eps)
+    for s in (1, -1):
+        Ps = (I + s * G5) / 2
+        A0 = Ps @ (2 * (I + s * S)) @ Ps
+        assert np.abs(Ps @ Dm @ Dm.conj().T @ Ps - k * (A0 + (mass * mass / k) * Ps)).max() < 1e-12
+        xs = (Ps @ x.ravel()).reshape(x.shape)
+        y = ov.overlap(U, ov.overlap_dag(U, xs, mass, params, small), mass, params, small)
+        sx = ov.sign_hw(U, xs, params, small)
+        want = k * 2 * (xs + s * (Ps @ sx.ravel()).reshape(x.shape)) + mass * mass * xs
+        got = (Ps @ y.ravel()).reshape(x.shape)
+        assert np.linalg.norm(got - want) <= 8 * delta * np.linalg.norm(xs) + 1e-12
+
+
 def test_free_field_overlap_closed_form():
     """Free field, periodic 4^4: D_ov(p) = 1 + D_w(p) / sqrt(M^2 + sum sin^2 p)."""
     dims = (4, 4, 4, 4)
