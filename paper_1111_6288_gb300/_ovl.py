@@ -222,7 +222,7 @@ class Context:
 
     @property
     def last_info(self):
-        """Summary of the last eigensolver call on this context."""
+        """Summary of the last solve (cycles, degrees, iterations) or eigensolver call on this context."""
         return lib().ov_last_info(self.handle).decode()
 
     @property

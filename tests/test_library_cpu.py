@@ -227,6 +227,10 @@ def test_multimass_solve_checks_its_arguments_on_the_host(ovl):
     assert call([0.1, -2.5]) == 1
     assert call([0.1, 0.2], tol=0.0) == 1
     assert call([0.1, 0.2]) == 9  # valid masses: the missing gauge field is reported
+    ctx = ovl.Context(ovl.Params(dims=(4, 4, 4, 4), eps=0.01, poly_degree=8, max_nrhs=1))
+    with pytest.raises(ValueError):
+        ovl.solve_overlap_multimass(ctx, None, None, [])  # the binding needs at least one mass
+    ctx.close()
     assert b"gauge" in L.ov_last_error(h)
     arr = (ctypes.c_double * 2)(0.1, 0.2)
     assert L.solve_overlap_multimass(h, 2, arr, None, a, a, 1, 1e-10, st, None) == 9  # state first
