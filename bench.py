@@ -208,7 +208,8 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "precision": "FP64 CPU oracle (numpy)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "per step: 2 oracle H_w applications at 16^3x32 plus one 50-vector projection, "
-                                   f"scaled to {2 * DEGREE + 1} Wilson applications per D_ov application"},
+                                   f"scaled to {2 * DEGREE + 1} Wilson applications per D_ov application",
+                         "paper_context": PAPER_CORE_EQUIVALENCE},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -246,6 +247,11 @@ def kernel_case(dims, precision="f32", shape=0):
     print("launch shapes timed:", ctx.tune_info)
     ctx.close()
 
+
+# The paper's GPU-to-CPU-core equivalence, for context only (other hardware, other codes).
+PAPER_CORE_EQUIVALENCE = ("about 30 Cray XT-5 cores per GPU for the paper's all-GPU code on its 2011 cluster "
+                          "(6 GB per GPU, 16 GPUs, QDR InfiniBand; CPU runs on 256 cores): 34 for the H_w "
+                          "eigensystem and 37 for the D_ov eigensystem (Sec. 3.1, abstract, conclusions)")
 
 MULTI_MASSES = (0.02, 0.03, 0.045, 0.06, 0.08, 0.1, 0.15)  # a ladder of seven masses (Sec. 4 uses seven)
 
@@ -526,7 +532,8 @@ def main():
         t_apply, t_w = oracle_sample(4)
         cpu = {"value": 1.0 / t_apply, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"4 oracle H_w applications at 16^3x32 ({t_w:.2f} s each) plus one 50-vector projection, "
-                         f"scaled to {2 * DEGREE + 1} Wilson applications per D_ov application"}
+                         f"scaled to {2 * DEGREE + 1} Wilson applications per D_ov application",
+               "gpu_over_oracle_core": value / (1.0 / t_apply), "paper_context": PAPER_CORE_EQUIVALENCE}
 
     if rank == 0:
         mean_mixed_s = max_ms / 1e3 / args.steps
