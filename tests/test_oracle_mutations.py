@@ -10,7 +10,8 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
-from oracle import chebyshev, dirac
+import synth
+from oracle import chebyshev, derivative, dirac
 from oracle import overlap as ov
 
 import test_oracle_pins as pins
@@ -92,3 +93,65 @@ def test_missing_projector_is_caught(setup, monkeypatch):
 
     monkeypatch.setattr(ov, "project", bad)
     assert pins.dense_split_error(setup) > 1e-3
+
+
+def test_dagger_without_gamma5_is_caught(setup, monkeypatch):
+    """D(m)^+ that applies sign^+ to psi instead of gamma5 psi."""
+    def bad(U, psi, mass, p, small, phase=0.0):
+        d_ov = psi + ov.sign_hw_dag(U, psi, p, small, phase)
+        return (1.0 - mass / 2.0) * d_ov + mass * psi
+
+    monkeypatch.setattr(ov, "overlap_dag", bad)
+    assert pins.shifted_family_error(setup, 0.3) > 1e-3
+
+
+def test_wrong_mass_normalisation_is_caught(setup, monkeypatch):
+    """D(m) = (1 + m/2) D_ov + m in place of (1 - m/2) D_ov + m."""
+    orig = ov.overlap
+
+    def bad(U, psi, mass, p, small, phase=0.0):
+        return orig(U, psi, mass, p, small, phase) + mass * (orig(U, psi, 0.0, p, small, phase))
+
+    monkeypatch.setattr(ov, "overlap", bad)
+    U, params, small, _, _, _ = setup
+    x = synth.gaussian_spinor((2, 2, 2, 2), 1, 41)[0]
+    assert np.linalg.norm(ov.overlap(U, x, 2.0, params, small) - 2.0 * x) > 1e-3
+    assert pins.shifted_family_error(setup, 0.3) > 1e-3
+
+
+def test_wrong_interval_map_is_caught(setup, monkeypatch):
+    """Y = (2 Q^2 - (1 - eps)) / (1 - eps): the interval [eps, 1] mapped off [-1, 1]."""
+    def bad(U, psi, p, phase=0.0):
+        q2 = ov.apply_Q(U, ov.apply_Q(U, psi, p, phase), p, phase)
+        return (2.0 * q2 - (1.0 - p.eps) * psi) / (1.0 - p.eps)
+
+    monkeypatch.setattr(ov, "apply_Y", bad)
+    assert pins.dense_split_error(setup) > 1e-3
+
+
+def test_recurrence_without_factor_two_is_caught(setup, monkeypatch):
+    """T_{k+1} = Y T_k - T_{k-1} in place of 2 Y T_k - T_{k-1}."""
+    def bad(U, psi, p, phase=0.0):
+        c = p.coeffs
+        t_prev, t_cur = psi, ov.apply_Y(U, psi, p, phase)
+        total = c[0] * t_prev + c[1] * t_cur
+        for k in range(2, len(c)):
+            t_prev, t_cur = t_cur, ov.apply_Y(U, t_cur, p, phase) - t_prev
+            total = total + c[k] * t_cur
+        return total
+
+    monkeypatch.setattr(ov, "apply_poly_Q2", bad)
+    assert pins.dense_split_error(setup) > 1e-3
+
+
+def test_flipped_field_derivative_is_caught(monkeypatch):
+    """dH_w/dphi with the wrong sign, against the central difference of H_w in phi."""
+    dims, bc, phase, h = (2, 2, 2, 4), (0, 1, 1, 0), 0.3, 1e-5
+    U = synth.random_su3_field(dims, 0.4, 2)
+    x = synth.gaussian_spinor(dims, 1, 3)[0]
+    fd = (dirac.hermitian_wilson(U, x, -1.5, bc, phase + h) - dirac.hermitian_wilson(U, x, -1.5, bc, phase - h)) / (2 * h)
+    good = derivative.dhw_dphi(U, x, bc, phase)
+    assert np.linalg.norm(good - fd) < 1e-6 * np.linalg.norm(fd)
+    orig = derivative.dwilson_dphi
+    monkeypatch.setattr(derivative, "dwilson_dphi", lambda *a, **k: -orig(*a, **k))
+    assert np.linalg.norm(derivative.dhw_dphi(U, x, bc, phase) - fd) > 0.5 * np.linalg.norm(fd)
