@@ -44,6 +44,11 @@ def _split(U, bc, phase, hw, n_ev, coeffs, eps):
 
 @pytest.mark.parametrize("n_ev", [0, 6])
 def test_split_sign_derivative_matches_finite_difference(n_ev):
+    assert split_derivative_error(n_ev) < 1e-6
+
+
+def split_derivative_error(n_ev):
+    """max |dF_DK - dF_FD| / max |dF_DK| on 2^3 x 4 (Dirichlet x and t, phase 0.15)."""
     dims, bc, phase = (2, 2, 2, 4), (0, 1, 1, 0), 0.15
     U = synth.random_su3_field(dims, 0.4, 5)
     site = synth.site_shape(dims) + (4, 3)
@@ -54,7 +59,7 @@ def test_split_sign_derivative_matches_finite_difference(n_ev):
     an = derivative.split_sign_derivative(H, dH, hw, n_ev, coeffs, eps)
     h = 1e-5
     fd = (_split(U, bc, phase + h, hw, n_ev, coeffs, eps) - _split(U, bc, phase - h, hw, n_ev, coeffs, eps)) / (2 * h)
-    assert np.abs(an - fd).max() / np.abs(an).max() < 1e-6
+    return np.abs(an - fd).max() / np.abs(an).max()
 
 
 def test_correlator_matches_loops_and_frobenius_norm():

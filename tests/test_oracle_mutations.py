@@ -14,6 +14,7 @@ import synth
 from oracle import chebyshev, derivative, dirac
 from oracle import overlap as ov
 
+import test_oracle_derivative as dpins
 import test_oracle_pins as pins
 
 
@@ -155,3 +156,14 @@ def test_flipped_field_derivative_is_caught(monkeypatch):
     orig = derivative.dwilson_dphi
     monkeypatch.setattr(derivative, "dwilson_dphi", lambda *a, **k: -orig(*a, **k))
     assert np.linalg.norm(derivative.dhw_dphi(U, x, bc, phase) - fd) > 0.5 * np.linalg.norm(fd)
+
+
+def test_derivative_without_chain_factor_is_caught(monkeypatch):
+    """dq/dtheta = P + theta^2 P' (the chain-rule factor 2 of d(theta^2) dropped)."""
+    def bad(theta, coeffs, eps):
+        dc = np.polynomial.chebyshev.chebder(coeffs) * (2.0 / (1.0 - eps))
+        x = theta ** 2
+        return chebyshev.eval_poly(coeffs, eps, x) + x * np.polynomial.chebyshev.chebval(chebyshev.to_y(x, eps), dc)
+
+    monkeypatch.setattr(derivative, "q_derivative", bad)
+    assert dpins.split_derivative_error(0) > 1e-3
