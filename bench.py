@@ -52,7 +52,7 @@ METRIC = "D_ov applies/s, dslash HBM GB/s, time-to-1e-10 solve (mixed vs FP64)"
 UNIT = "D_ov applies/s"
 WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV}, m={MASS}, tol={TOL}"
 # ncu, one pass, no replay, caches as the solve leaves them: DRAM bytes of the FP32 Wilson kernel
-# over its algorithmic bytes in the timed region of this bench (profiles/solve_16x32x32_launch_list.md):
+# over its algorithmic bytes in the timed region of this bench (profiles/solve_16x16x16x32_launch_list.md):
 # the loop's vectors and links stay in L2.  Set to None whenever the kernel changes until re-measured.
 DRAM_OVER_ALGORITHMIC = 0.14
 
