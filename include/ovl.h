@@ -230,23 +230,26 @@ int apply_overlap(ov_ctx* ctx, const void* in, void* out, int nrhs, double mass,
 #define OV_NOALLOC_SCRATCH_BYTES (8u << 20)
 
 /* out = D_w in (hermitian = 0) or H_w in (hermitian = 1), like apply_wilson, for callers
- * that cannot allocate device memory: code running while a CUDA graph is captured,
- * applications whose memory manager owns every device allocation, real-time loops with
- * a fixed memory budget.  It needs no context and calls no cudaMalloc, cudaFree or
- * allocating library routine.  The paper has no counterpart to this call.
+ * that cannot allocate device memory: applications whose memory manager owns every device
+ * allocation, real-time loops with a fixed memory budget, code that must not make the
+ * device synchronisation cudaMalloc and cudaFree can cause.  It needs no context and calls
+ * no cudaMalloc, cudaFree or allocating library routine.  The paper has no counterpart to
+ * this call.
  * dims: host [4] (Lx, Ly, Lz, Lt), bc: host [4] OV_BC_*, U: device gauge field
  * [4][site][3][3] complex128, in/out: device spinors [nrhs][site][4][3] complex128,
- * in != out, phase: host [nrhs] (NULL = all zero).  FP64 arithmetic, the same kernels
- * as apply_wilson.
+ * in != out, phase: host [nrhs] (NULL = all zero), 1 <= nrhs <= 256; the phases are passed
+ * to the GPU by value in a kernel argument, so no host array is read after the call
+ * returns.  FP64 arithmetic, the same kernels as apply_wilson.
  * Scratch: one file-scope device array of OV_NOALLOC_SCRATCH_BYTES, held by every GPU
  * that loads the library until the process exits; a call needs
  * 16 (36 V + 24 V nrhs) bytes plus alignment (V = sites), so one rhs fits up to about
- * 8700 sites (8^4 = 4096); larger requests return OV_ERR_ARG with a message in
- * ov_last_error(NULL) before any GPU work.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current): make that
- * first call before any stream capture.  Every call shares the array; each call writes
- * every element it reads, so nothing needs clearing, but calls that overlap on the GPU
- * (other streams or host threads) race on it and must be serialised by the caller. */
+ * 8700 sites (8^4 = 4096); larger requests (extents whose product would overflow
+ * included) return OV_ERR_ARG with a message in ov_last_error(NULL) before any GPU work.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current): make that first call before any stream capture.  Every call
+ * shares the array; each call writes every element it reads, so nothing needs clearing,
+ * but calls that overlap on the GPU (other streams or host threads) race on it and must
+ * be serialised by the caller. */
 int apply_wilson_noalloc(const int dims[4], const int bc[4], double m0, const void* U, const void* in,
                          void* out, int nrhs, const double* phase, int hermitian, ov_stream_t stream);
 

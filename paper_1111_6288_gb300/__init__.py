@@ -16,6 +16,16 @@ from ._ovl import (  # noqa: F401
     OV_BC_ANTIPERIODIC,
     OV_BC_DIRICHLET,
     OV_BC_PERIODIC,
+    OV_ERR_ARG,
+    OV_ERR_BREAKDOWN,
+    OV_ERR_CUDA,
+    OV_ERR_NAN,
+    OV_ERR_NO_BANK,
+    OV_ERR_NOT_CONVERGED,
+    OV_ERR_OOM,
+    OV_ERR_STATE,
+    OV_ERR_TIMEOUT,
+    OV_OK,
     OV_PREC_BF16,
     OV_PREC_F16,
     OV_PREC_F32,

@@ -12,6 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "libovl.so")
 
 OV_OK = 0
+(OV_ERR_ARG, OV_ERR_CUDA, OV_ERR_OOM, OV_ERR_NOT_CONVERGED, OV_ERR_BREAKDOWN, OV_ERR_NAN, OV_ERR_TIMEOUT,
+ OV_ERR_NO_BANK, OV_ERR_STATE) = range(1, 10)
 OV_BC_PERIODIC, OV_BC_ANTIPERIODIC, OV_BC_DIRICHLET = 0, 1, 2
 OV_PREC_F64, OV_PREC_F32, OV_PREC_F16, OV_PREC_BF16 = 0, 1, 2, 3
 OV_C128, OV_C64 = 0, 1

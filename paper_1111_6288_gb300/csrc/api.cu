@@ -903,9 +903,10 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     for (int mu = 0; mu < 4; ++mu) {
         if (p->dims[mu] < 2) return fail(c, OV_ERR_ARG, "dims[%d] = %d < 2", mu, p->dims[mu]);
         if (p->bc[mu] < 0 || p->bc[mu] > 2) return fail(c, OV_ERR_ARG, "bc[%d] = %d invalid", mu, p->bc[mu]);
+        // checked before each product (V <= 2^30 / 12 and an int extent cannot overflow 64 bits)
         V *= p->dims[mu];
+        if (V > (1LL << 30) / 12) return fail(c, OV_ERR_ARG, "lattice too large for 32-bit site indexing");
     }
-    if (V > (1LL << 30) / 12) return fail(c, OV_ERR_ARG, "lattice too large for 32-bit site indexing");
     if (!(p->eps > 0.0 && p->eps < 1.0)) return fail(c, OV_ERR_ARG, "eps = %g outside (0, 1)", p->eps);
     if (p->poly_degree < 1 || p->poly_degree > 100000)
         return fail(c, OV_ERR_ARG, "poly_degree = %d outside [1, 100000]", p->poly_degree);

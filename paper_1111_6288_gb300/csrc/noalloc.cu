@@ -1,10 +1,10 @@
 // apply_wilson_noalloc: the Wilson operator for callers that cannot allocate
 // device memory.
 //
-// Some callers may not call cudaMalloc at all: code running while a CUDA graph
-// is being captured (allocation is not a capturable operation), host
-// applications whose memory manager owns every device allocation and forbids
-// other allocators, and real-time loops with a fixed memory budget.  This entry
+// Some callers may not call cudaMalloc at all: host applications whose memory
+// manager owns every device allocation and forbids other allocators, real-time
+// loops with a fixed memory budget, and code that must not make the implicit
+// device synchronisation that cudaMalloc and cudaFree can cause.  This entry
 // point serves them: it takes the gauge field and the spinors in the caller's
 // buffers (ABI layouts, complex128) and keeps its packed copies in one
 // file-scope device array of fixed size instead of allocating.  The paper has
@@ -14,11 +14,13 @@
 // held by every GPU that loads it until the process exits.  Its device address
 // is looked up with cudaGetSymbolAddress once per device, by the first call on
 // that device (with that device current); that first call should therefore
-// come before any stream capture.  All calls share the array and it keeps the
-// last call's contents: every element a call reads is first written by that
-// same call (packed links, packed input, phases, packed output), so nothing
-// needs clearing, but calls whose work overlaps on the GPU (different streams,
-// or different host threads) race on the array and must be serialised by the
+// come before any stream capture.  The field phases travel by value in a kernel
+// argument that writes them into the array, so the call reads no host memory
+// after it returns.  All calls share the array and it keeps the last call's
+// contents: every element a call reads is first written by that same call
+// (phases, packed links, packed input, packed output), so nothing needs
+// clearing, but calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on the array and must be serialised by the
 // caller.
 #include <cuda_runtime.h>
 
@@ -62,6 +64,18 @@ int reject(int code, const char* msg) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// The per-rhs field phases, by value (kMaxRhs doubles = 2 KiB of kernel arguments).
+struct PhaseArgs {
+    double v[ovl::kMaxRhs];
+};
+
+__global__ void store_phases_k(PhaseArgs a, int n, double* __restrict__ out) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) out[j] = a.v[j];
+}
+
+// Most sites any call can use (one rhs: 16 (36 V + 24 V) bytes of scratch plus alignment).
+constexpr long long kMaxSites = (long long)(kScratchBytes / (sizeof(double2) * 60));
+
 }  // namespace
 
 extern "C" int apply_wilson_noalloc(const int dims[4], const int bc[4], double m0, const void* U, const void* in,
@@ -77,6 +91,16 @@ extern "C" int apply_wilson_noalloc(const int dims[4], const int bc[4], double m
         if (bc[mu] < 0 || bc[mu] > 2) return reject(OV_ERR_ARG, "apply_wilson_noalloc: invalid boundary condition");
         g.L[mu] = dims[mu];
         g.bcf[mu] = bc[mu] == OV_BC_PERIODIC ? 1.0 : (bc[mu] == OV_BC_ANTIPERIODIC ? -1.0 : 0.0);
+        // bounded before the next product, so that V never overflows: any partial product above
+        // the array's capacity already rules the request out
+        if (dims[mu] > kMaxSites || V * dims[mu] > kMaxSites) {
+            char buf[256];
+            snprintf(buf, sizeof(buf),
+                     "apply_wilson_noalloc: the lattice has more sites than the fixed %zu bytes of scratch hold "
+                     "(at most about %lld sites for one rhs)",
+                     kScratchBytes, kMaxSites);
+            return reject(OV_ERR_ARG, buf);
+        }
         V *= dims[mu];
     }
     if (phase)
@@ -93,7 +117,7 @@ extern "C" int apply_wilson_noalloc(const int dims[4], const int bc[4], double m
         snprintf(buf, sizeof(buf),
                  "apply_wilson_noalloc: %lld sites x %d rhs need %zu bytes of scratch, more than the fixed %zu "
                  "(at most about %lld sites for one rhs)",
-                 V, nrhs, need, kScratchBytes, (long long)(kScratchBytes / (c16 * 60)));
+                 V, nrhs, need, kScratchBytes, kMaxSites);
         return reject(OV_ERR_ARG, buf);
     }
     g.V = (int)V;
@@ -111,8 +135,10 @@ extern "C" int apply_wilson_noalloc(const int dims[4], const int bc[4], double m
     void* xin = p + b_phase + b_links;
     void* xout = p + b_phase + b_links + b_spin;
     if (phase) {
-        e = cudaMemcpyAsync(d_phase, phase, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return reject(OV_ERR_CUDA, "apply_wilson_noalloc: phase upload failed");
+        PhaseArgs pa;
+        for (int j = 0; j < nrhs; ++j) pa.v[j] = phase[j];
+        store_phases_k<<<1, 128, 0, s>>>(pa, nrhs, d_phase);
+        ovl::count_launch();
     }
     ovl::launch_pack_gauge<double>(U, OV_C128, links, g, s);
     ovl::launch_pack_spinor<double>(in, OV_C128, xin, g.V, nrhs, s);

@@ -265,4 +265,19 @@ def test_noalloc_rejects_oversize_without_a_gpu(ovl):
     bc = (ctypes.c_int * 4)(0, 0, 0, 1)
     rc = L.apply_wilson_noalloc(d, bc, -1.5, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(64), 1, None, 1,
                                 None)
-    assert rc == 1 and b"scratch" in L.ov_last_error(None)
+    assert rc == ovl.OV_ERR_ARG and b"scratch" in L.ov_last_error(None)
+
+
+@pytest.mark.parametrize("dims", [(2**31 - 1, 2**31 - 1, 2**31 - 1, 2**31 - 1), (2, 2**31 - 1, 2**30, 4),
+                                  (65536, 65536, 65536, 65536)])
+def test_extents_near_int_max_are_rejected_without_overflow(ovl, dims):
+    """Extents whose product overflows 64 bits (or wraps to a small value) are rejected on the host."""
+    L = ovl.lib()
+    d = (ctypes.c_int * 4)(*dims)
+    bc = (ctypes.c_int * 4)(0, 0, 0, 1)
+    rc = L.apply_wilson_noalloc(d, bc, -1.5, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(64), 1, None, 1,
+                                None)
+    assert rc == ovl.OV_ERR_ARG and b"scratch" in L.ov_last_error(None)
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.Context(ovl.Params(dims=dims))
+    assert e.value.code == ovl.OV_ERR_ARG

@@ -1,9 +1,10 @@
 """apply_wilson_noalloc against apply_wilson, through the C ABI.
 
 apply_wilson_noalloc is the Wilson operator for callers that cannot allocate
-device memory (code running under CUDA graph capture, applications whose
-memory manager owns every device allocation, real-time loops with a fixed
-budget): it works in one fixed file-scope device array instead of allocating.
+device memory (applications whose memory manager owns every device
+allocation, real-time loops with a fixed budget, code that must not make the
+device synchronisation cudaMalloc and cudaFree can cause): it works in one
+fixed file-scope device array instead of allocating.
 These checks run two calls in a row on different lattices and inputs (so the
 second call starts from the first call's leftovers in the shared array) and
 compare each with apply_wilson, the context-based entry point, to the FP64
@@ -94,5 +95,5 @@ def test_noalloc_rejects_requests_beyond_its_array(P):
     rc = P.lib().apply_wilson_noalloc(d, b, M0, C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()),
                                       C.c_void_p(dummy.data_ptr() + 16), 1, None, 1,
                                       C.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert rc == 1
+    assert rc == P.OV_ERR_ARG
     assert b"scratch" in P.lib().ov_last_error(None)
