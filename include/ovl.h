@@ -349,6 +349,21 @@ int ov_apply_dHdphi(ov_ctx* ctx, const void* in, void* out, int nrhs, const doub
 int ov_apply_dDdphi(ov_ctx* ctx, const void* in, void* out, int nrhs, double mass, const double* phase,
                     ov_stream_t stream);
 
+/* Derivative of the pion correlator with respect to the field E (Sec. 4: the energy shifts come
+ * from correlators at several field values; this is their E-derivative through the solve).
+ * S: device [nrhs][site][4][3] complex128, the propagator columns S_j = D(m)^-1 b_j at the phase
+ * phi = charge E (a small-space bank registered for phi when phi != 0).  u_j = dD(m)/dphi S_j as
+ * ov_apply_dDdphi computes it.  dC: host [Lt + 1].
+ *  lam == NULL (tangent): dC[t] = dC(t)/dE = 2 Re sum_j <S_j, dS_j/dE>_t with
+ *    dS_j/dE = -charge D(m)^-1 u_j, solved here to tol as solve_overlap does (x0 = 0);
+ *  lam != NULL (adjoint): dC[t] = -2 charge Re sum_j <lam_j, u_j>_t with lam device [nrhs][site][4][3]
+ *    complex128 (for lam = gamma5 D(m)^-1 gamma5 (g o S), the adjoint solution of a loss L with
+ *    dL/dC(t) = g(t), the sum over t is dL/dE); tol unused.
+ *  dC[Lt] = sum over t of dC[t].  <a, b>_t sums conj(a) b over the sites of time slice t.
+ * Synchronises the stream. */
+int ov_dcorr_dE(ov_ctx* ctx, double mass, double charge, double E, const void* S, const void* lam, int nrhs,
+                double tol, double* dC, ov_stream_t stream);
+
 /* Pion correlator C(t) = sum_rhs sum_{x,y,z} sum_{spin,colour} |S|^2 of propagator columns
  * S (device [nrhs][site][4][3]); C: host [Lt].  Synchronises the stream. */
 int ov_correlator(ov_ctx* ctx, const void* S, int nrhs, double* C, ov_stream_t stream);

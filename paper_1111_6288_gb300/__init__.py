@@ -42,6 +42,7 @@ from ._ovl import (  # noqa: F401
     chebyshev_coeffs,
     correlator,
     correlator_jacobian,
+    dcorr_dE,
     clear_overlap_deflation,
     deflate,
     eigensolve_Q,

@@ -104,6 +104,7 @@ _SIGNATURES = {
     "ov_apply_dHdphi": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
     "ov_apply_dDdphi": (_I, [_VP, _VP, _VP, _I, _D, _DP, _VP]),
     "ov_correlator": (_I, [_VP, _VP, _I, _DP, _VP]),
+    "ov_dcorr_dE": (_I, [_VP, _D, _D, _D, _VP, _VP, _I, _D, _DP, _VP]),
     "ov_timeslice_scale": (_I, [_VP, _VP, _VP, _I, _DP, _I, _VP]),
     "ov_inner": (_I, [_VP, _VP, _VP, _I, _I, _DP, _VP]),
 }
@@ -557,19 +558,30 @@ def _solve_columns(ctx, b, mass, phase, tol):
     return x
 
 
-def correlator_jacobian(ctx: Context, sources, E, charge, mass, tol=1e-12):
-    """dC(t)/dE at field E by the tangent of the solve: dS = -D^-1 (dD/dphi) S q,
-    dC(t) = 2 Re sum <S, dS>_t.  Returns (C, dC/dE) as numpy arrays [Lt]."""
+def dcorr_dE(ctx: Context, S, mass, charge, E, lam=None, tol=1e-12, stream=None):
+    """ov_dcorr_dE: without lam, dC(t)/dE (numpy [Lt]) of C(t) = sum |S|^2_t through the tangent
+    solve; with lam (the adjoint solution), the adjoint form's per-timeslice terms.  Returns
+    (per-timeslice values [Lt], their sum)."""
     import torch
 
+    n = ctx._check_spinor(S, "S", dtype=torch.complex128)
+    lptr = None
+    if lam is not None:
+        if ctx._check_spinor(lam, "lam", dtype=torch.complex128) != n:
+            raise ValueError("lam must have as many columns as S")
+        lptr = C.c_void_p(lam.data_ptr())
+    out = np.zeros(ctx.dims[3] + 1)
+    _check(lib().ov_dcorr_dE(ctx.handle, float(mass), float(charge), float(E), C.c_void_p(S.data_ptr()), lptr, n,
+                             float(tol), out.ctypes.data_as(_DP), _stream(stream)), ctx.handle)
+    return out[:-1], float(out[-1])
+
+
+def correlator_jacobian(ctx: Context, sources, E, charge, mass, tol=1e-12):
+    """C(t) and dC(t)/dE at field E (phase charge * E), the derivative by the tangent of the solve
+    (ov_dcorr_dE).  Returns numpy arrays [Lt]."""
     phase = charge * float(E)
     S = _solve_columns(ctx, sources, mass, phase, tol)
-    C = correlator(ctx, S)
-    dDS = torch.empty_like(S)
-    apply_dDdphi(ctx, S, dDS, mass, phase=[phase] * S.shape[0])
-    dS = _solve_columns(ctx, dDS, mass, phase, tol)  # D^-1 dD S
-    ip = inner(ctx, S, dS, per_timeslice=True)
-    return C, -2.0 * charge * np.real(ip).sum(axis=0)
+    return correlator(ctx, S), dcorr_dE(ctx, S, mass, charge, E, tol=tol)[0]
 
 
 def _make_correlator_function():
@@ -579,29 +591,26 @@ def _make_correlator_function():
         """C(t; E) of the point-source propagators at field E, phase phi = charge * E.
 
         forward: one solve per source and the correlator.  backward: the adjoint solve
-        lam = D^-+ (g o S) = gamma5 D^-1 gamma5 (g o S) and dL/dE = -2 charge Re sum <lam, dD/dphi S>.
+        lam = D^-+ (g o S) = gamma5 D^-1 gamma5 (g o S), then dL/dE from ov_dcorr_dE.
         """
 
         @staticmethod
         def forward(fctx, E, ctx, sources, charge, mass, tol):
             phase = charge * float(E)
             S = _solve_columns(ctx, sources, mass, phase, tol)
-            fctx.ovl = (ctx, S, charge, mass, tol, phase)
+            fctx.ovl = (ctx, S, charge, mass, tol, phase, float(E))
             return torch.from_numpy(correlator(ctx, S)).to(E.dtype)
 
         @staticmethod
         def backward(fctx, gC):
-            ctx, S, charge, mass, tol, phase = fctx.ovl
+            ctx, S, charge, mass, tol, phase, E = fctx.ovl
             g = gC.detach().cpu().double().numpy()
             w = torch.empty_like(S)
             timeslice_scale(ctx, S, w, g, gamma5=True)        # gamma5 (g o S)
             y = _solve_columns(ctx, w, mass, phase, tol)
             lam = torch.empty_like(S)
             timeslice_scale(ctx, y, lam, np.ones(ctx.dims[3]), gamma5=True)
-            dDS = torch.empty_like(S)
-            apply_dDdphi(ctx, S, dDS, mass, phase=[phase] * S.shape[0])
-            ip = inner(ctx, lam, dDS)
-            gE = -2.0 * charge * float(np.real(ip).sum())
+            _, gE = dcorr_dE(ctx, S, mass, charge, E, lam=lam)
             return torch.tensor(gE, dtype=gC.dtype), None, None, None, None, None
 
     return PionCorrelator

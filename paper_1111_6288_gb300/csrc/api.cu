@@ -2737,6 +2737,69 @@ int ov_apply_dDdphi(ov_ctx* c, const void* in, void* out, int nrhs, double mass,
     return OV_OK;
 }
 
+int ov_dcorr_dE(ov_ctx* c, double mass, double charge, double E, const void* S, const void* lam, int nrhs, double tol,
+                double* dC, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    if (!c->gauge_set) return fail(c, OV_ERR_STATE, "no gauge field set (call ov_set_gauge first)");
+    if (!S || !dC) return fail(c, OV_ERR_ARG, "null S or dC");
+    if (nrhs < 1 || nrhs > c->p.max_nrhs)
+        return fail(c, OV_ERR_ARG, "nrhs = %d outside [1, max_nrhs = %d]", nrhs, c->p.max_nrhs);
+    if (!std::isfinite(mass) || !std::isfinite(charge) || !std::isfinite(E))
+        return fail(c, OV_ERR_ARG, "mass, charge and E must be finite");
+    if (!lam && !(tol > 0.0)) return fail(c, OV_ERR_ARG, "tol must be > 0 for the tangent solve");
+    if (lam == S) return fail(c, OV_ERR_ARG, "lam and S must be different buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int V = c->g.V, Lt = c->g.L[3];
+    const long long n12 = 12LL * V;
+    const double phase = charge * E;
+    SysSet Sph = make_sys(nrhs, nullptr);
+    Sph.phase.assign(nrhs, phase);
+    TRY(phase_check(c, Sph));
+    // u = dD(m)/dphi S = (1 - m/2) gamma5 dF/dphi S (internal FP64 layout, then ABI)
+    void *X, *Y, *U;
+    TRY(workspace(c, "dc_X", OV_PREC_F64, nrhs, &X));
+    TRY(workspace(c, "dc_Y", OV_PREC_F64, nrhs, &Y));
+    TRY(workspace(c, "dc_U", OV_PREC_F64, nrhs, &U));  // ABI complex128 [nrhs][site][4][3]
+    launch_pack_spinor<double>(S, OV_C128, X, V, nrhs, s);
+    CKL();
+    TRY(dsign_dphi(c, X, Sph, Y, s));
+    launch_gamma5<double>(Y, X, V, nrhs, s);
+    launch_scale<double>(1.0 - 0.5 * mass, X, Y, n12 * nrhs, s);
+    launch_unpack_spinor<double>(Y, U, OV_C128, V, nrhs, s);
+    CKL();
+    const void* left = lam;  // <left, right>_t
+    const void* right = U;
+    if (!lam) {
+        // tangent: dS/dE = -q D(m)^-1 u; w = D(m)^-1 u solved here, then <S, w>_t
+        void* Wsol;
+        TRY(workspace(c, "dc_W", OV_PREC_F64, nrhs, &Wsol));
+        CK(cudaMemsetAsync(Wsol, 0, vec_bytes(c, OV_PREC_F64) * nrhs, s));
+        ov_solve_stats st{};
+        const int rc = c->p.inner_precision == OV_PREC_F64 ? solve_impl<double>(c, mass, Sph, U, Wsol, tol, &st, s)
+                                                           : solve_impl<float>(c, mass, Sph, U, Wsol, tol, &st, s);
+        if (rc != OV_OK) return rc;
+        left = S;
+        right = Wsol;
+    }
+    const int nseg = nrhs * Lt;
+    const long long seg = 12LL * (V / Lt);  // complex numbers per (rhs, timeslice) in the ABI layout
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * nseg, nseg));
+    std::vector<double2> ip(nseg);
+    dot_rhs<double>(left, right, seg, nseg, ip.data(), c->d_partial, c->d_red, s);
+    CKL();
+    // dC(t) = 2 Re sum_j <S_j, dS_j/dE>_t = -2 q Re sum_j <S_j, w_j>_t (tangent), or the adjoint
+    // form's per-timeslice terms -2 q Re sum_j <lam_j, u_j>_t; dC[Lt] = their sum over t
+    double total = 0.0;
+    for (int t = 0; t < Lt; ++t) {
+        double acc = 0.0;
+        for (int j = 0; j < nrhs; ++j) acc += ip[(size_t)j * Lt + t].x;
+        dC[t] = -2.0 * charge * acc;
+        total += dC[t];
+    }
+    dC[Lt] = total;
+    return OV_OK;
+}
+
 int ov_correlator(ov_ctx* c, const void* S, int nrhs, double* C, ov_stream_t stream) {
     if (!c || !S || !C || nrhs < 1) return c ? fail(c, OV_ERR_ARG, "invalid correlator arguments") : OV_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;

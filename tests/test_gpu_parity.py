@@ -331,3 +331,36 @@ def test_eigensolver_matches_dense(P, lat4):
         r = dirac.hermitian_wilson(d["U"], Vh[i], M0, oracle_bc(d["bc"])) / d["hw"] - lam[i] * Vh[i]
         assert np.linalg.norm(r) < 1e-10
     ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# sign function at the measured workload's polynomial (n = 527, sqrt(eps) = 0.02)
+# ---------------------------------------------------------------------------
+
+def test_sign_f64_at_the_bench_degree_matches_oracle(P):
+    """FP64 sign(H_w) on 8^4 with the bench's polynomial (minimax, n = 527 on [4e-4, 1]) and
+    boundary conditions, links exp(i 0.2 H) as in the 16^3 x 32 workload, and a 16-vector small
+    space that is not an invariant subspace (random orthonormal vectors, mixed signs), so that the
+    projection, the 1054 Wilson applications of the recurrence and the final Q all enter.  The
+    lowest |Q| of such a near-free field (the doublers, ~0.08) lies inside the polynomial's
+    interval, so the recurrence stays in [-1, 1] and the two implementations agree to 1e-12."""
+    from oracle import chebyshev
+
+    dims, bc, degree, eps, n_ev = (8, 8, 8, 8), (0, 0, 0, 1), 527, 0.02 ** 2, 16
+    U = synth.random_su3_field(dims, 0.2, 0)
+    rng = np.random.default_rng(21)
+    site = synth.site_shape(dims) + (4, 3)
+    A = rng.standard_normal((n_ev, int(np.prod(site)))) + 1j * rng.standard_normal((n_ev, int(np.prod(site))))
+    Qm, _ = np.linalg.qr(A.T)
+    V = np.ascontiguousarray(Qm.T.reshape((n_ev,) + site))
+    lam = np.where(np.arange(n_ev) % 3 == 0, -1.0, 1.0) * (0.05 + 0.001 * np.arange(n_ev))
+    ctx = P.Context(P.Params(dims=dims, bc=bc, m0=M0, eps=eps, poly_degree=degree, poly_kind=1, max_nrhs=1))
+    ctx.set_gauge(to_dev(U))
+    P.deflate(ctx, to_dev(V), lam)
+    x = synth.gaussian_spinor(dims, 1, 5)
+    got = gpu_apply(P, ctx, P.apply_sign_Hw, x)
+    cm, _ = chebyshev.minimax_coeffs(degree, eps)
+    p = ov.OverlapParams(m0=M0, hw_norm=ctx.hw_norm, eps=eps, degree=degree, bc=oracle_bc(bc), coeffs=cm)
+    want = ov.sign_hw(U, x[0], p, ov.SmallSpace.from_eigenpairs(V, lam))
+    assert relerr(got[0], want) < F64_TOL
+    ctx.close()

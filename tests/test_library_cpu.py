@@ -180,6 +180,9 @@ def test_calls_before_a_gauge_field_are_rejected_on_the_host(ovl):
     assert b"gauge" in L.ov_last_error(h)
     assert L.apply_sign_Hw(h, a, b, 1, None, None) == 9
     assert L.apply_overlap(h, a, b, 1, 0.1, None, None) == 9
+    dC = (ctypes.c_double * 5)()
+    assert L.ov_dcorr_dE(h, 0.1, 2.0 / 3.0, 1e-4, a, None, 1, 1e-10, dC, None) == ovl.OV_ERR_STATE
+    assert L.ov_dcorr_dE(None, 0.1, 2.0 / 3.0, 1e-4, a, None, 1, 1e-10, dC, None) == ovl.OV_ERR_ARG
     L.ov_destroy(h)
 
 
