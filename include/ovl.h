@@ -74,12 +74,13 @@ enum { OV_BC_PERIODIC = 0, OV_BC_ANTIPERIODIC = 1, OV_BC_DIRICHLET = 2 };
 
 /* Arithmetic of operator applications. F64: FP64 storage and arithmetic.
  * F32: FP32 storage and arithmetic (reductions accumulate in FP64).
- * F16, BF16 (precision only, not inner_precision): the gauge links and the vectors of the
- * Chebyshev recurrence are stored in 16 bits (FP16 with one FP32 scale per site, or BF16)
- * and computed in FP32; the small-space projection, the final application of H_w and the
- * caller arrays (complex64) stay FP32.  The result carries the 16-bit rounding (relative
- * error ~1e-3 for FP16, ~1e-2 for BF16), which the solver's defect correction cannot absorb
- * at light quark masses, so solve_overlap keeps FP32 or FP64 in its inner loop. */
+ * F16, BF16: the gauge links and the vectors of the Chebyshev recurrence are stored in 16
+ * bits (FP16 with one FP32 scale per site, or BF16) and computed in FP32; the small-space
+ * projection, the final application of H_w and the caller arrays (complex64) stay FP32.
+ * The result carries the 16-bit rounding (relative error ~1e-3 for FP16, ~1e-2 for BF16).
+ * As inner_precision of the solver a 16-bit format is allowed only in a context of that
+ * precision (the 16-bit links exist there); the solver's FP64 defect correction then
+ * removes that rounding over more outer cycles. */
 enum { OV_PREC_F64 = 0, OV_PREC_F32 = 1, OV_PREC_F16 = 2, OV_PREC_BF16 = 3 };
 
 /* Element type of caller arrays. */
@@ -96,7 +97,9 @@ typedef struct ov_params {
     const double* coeffs; /* host [n+1] coefficients of P in the T_k basis, or NULL for the
                              Chebyshev interpolant of x^{-1/2} (see ov_chebyshev_coeffs) */
     int precision;        /* OV_PREC_* of apply_wilson / apply_sign_Hw / apply_overlap */
-    int inner_precision;  /* OV_PREC_* of the inner CG in solve_overlap (FP64 outer loop) */
+    int inner_precision;  /* OV_PREC_* of the inner CG in solve_overlap (FP64 outer loop): F64, F32,
+                             or the 16-bit format of `precision` (FP32 arithmetic, 16-bit storage
+                             of the polynomial loops of the inner CG and of its correction) */
     int max_nrhs;         /* largest nrhs of any call, >= 1 */
     int max_iter;         /* cap on inner CG iterations per solve (<= 0: 100000) */
     double inner_tol;     /* relative tolerance of each inner solve (<= 0: default,
@@ -283,6 +286,11 @@ int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_ite
  * sector), then the correction D(m)^+ y.  stats: host, may be NULL. */
 int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, void* x,
                   int nrhs, double tol, ov_solve_stats* stats, ov_stream_t stream);
+
+/* Change the inner precision of later solves (values as ov_params.inner_precision).  The D_ov
+ * deflation spaces serve every inner precision: FP32 and 16-bit inner solves use their FP32
+ * vectors and the FP64 low-mode step, FP64 inner solves their FP64 vectors. */
+int ov_set_inner_precision(ov_ctx* ctx, int inner_precision);
 
 /* Most masses one solve_overlap_multimass call takes. */
 #define OV_MAX_MASSES 32

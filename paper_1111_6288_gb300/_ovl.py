@@ -99,6 +99,7 @@ _SIGNATURES = {
     "apply_wilson_noalloc": (_I, [C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _VP, _VP, _VP, _I, _DP, _I, _VP]),
     "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
     "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
+    "ov_set_inner_precision": (_I, [_VP, _I]),
     "solve_overlap": (_I, [_VP, _D, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),
     "solve_overlap_multimass": (_I, [_VP, _I, _DP, _DP, _VP, _VP, _I, _D, C.POINTER(_SolveStats), _VP]),
     "ov_apply_dHdphi": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
@@ -273,6 +274,11 @@ class Context:
         if tuple(t.shape[1:]) != self.site_shape + (4, 3):
             raise ValueError(f"{name} has shape {tuple(t.shape)}, expected (nrhs,) + {self.site_shape + (4, 3)}")
         return t.shape[0]
+
+    def set_inner_precision(self, precision):
+        """Inner-CG precision of later solves (OV_PREC_F64, OV_PREC_F32, or the context's 16-bit format)."""
+        _check(lib().ov_set_inner_precision(self.handle, int(precision)), self.handle)
+        self.params.inner_precision = int(precision)
 
     def set_profiling(self, on=True):
         """Record CUDA events around every polynomial (Clenshaw) loop."""

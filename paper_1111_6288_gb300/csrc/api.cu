@@ -600,6 +600,16 @@ int overlap_op(ov_ctx* c, const void* X, const SysSet& S, double mass, bool dagg
     return sign_pipeline<R, ST>(c, X, S, dagger, fin, out, s, degree);
 }
 
+// The solver's inner loop runs in FP64, FP32, or with the 16-bit storage of the context's own precision
+// (the 16-bit links exist only in an FP16 / BF16 context).
+int check_inner_precision(ov_ctx* c, const ov_params* p, int inner) {
+    if (inner == OV_PREC_F64 || inner == OV_PREC_F32) return OV_OK;
+    if ((inner == OV_PREC_F16 || inner == OV_PREC_BF16) && inner == p->precision) return OV_OK;
+    return fail(c, OV_ERR_ARG,
+                "inner_precision = %d invalid (FP64, FP32, or the 16-bit format of the context's precision %d)",
+                inner, p->precision);
+}
+
 int check_ready(ov_ctx* c, const void* in, const void* out, int nrhs) {
     if (!c) return OV_ERR_ARG;
     if (!c->gauge_set) return fail(c, OV_ERR_STATE, "no gauge field set (call ov_set_gauge first)");
@@ -912,11 +922,7 @@ int ov_create(const ov_params* p, ov_ctx** out) {
         return fail(c, OV_ERR_ARG, "poly_degree = %d outside [1, 100000]", p->poly_degree);
     if (p->precision < OV_PREC_F64 || p->precision > OV_PREC_BF16)
         return fail(c, OV_ERR_ARG, "precision = %d invalid", p->precision);
-    if (p->inner_precision != OV_PREC_F64 && p->inner_precision != OV_PREC_F32)
-        return fail(c, OV_ERR_ARG,
-                    "inner_precision = %d invalid (the solver's inner loop runs in FP64 or FP32: 16-bit "
-                    "storage limits the operator to ~1e-3, too coarse for its defect correction)",
-                    p->inner_precision);
+    TRY(check_inner_precision(c, p, p->inner_precision));
     if (p->max_nrhs < 1 || p->max_nrhs > kMaxRhs / 2)
         return fail(c, OV_ERR_ARG, "max_nrhs = %d outside [1, %d]", p->max_nrhs, kMaxRhs / 2);
     if (!std::isfinite(p->m0)) return fail(c, OV_ERR_ARG, "m0 not finite");
@@ -1345,11 +1351,14 @@ int dspace_prepare64(ov_ctx* c, DefSpace& sp, double mass, cudaStream_t s) {
     return OV_OK;
 }
 
-// out (host, n) = Einv * (A_i^+ v for the n vectors A of the space), A = AWm or W.
+// out (host, n) = Einv * (A_i^+ v for the n vectors A of the space), A = AWm or W, in precision R
+// (FP32: the FP32 vectors and Einv; FP64: the FP64 vectors and Einv64).
+template <typename R = float>
 int dspace_coeffs(ov_ctx* c, DefSpace& sp, const void* A, const void* v, std::vector<HostCplx>& out, bool apply_einv,
                   cudaStream_t s) {
     std::vector<HostCplx> g;
-    TRY(gram_host<float>(c, A, sp.n, v, 1, g, s));
+    TRY(gram_host<R>(c, A, sp.n, v, 1, g, s));
+    const std::vector<HostCplx>& Einv = std::is_same<R, double>::value ? sp.Einv64 : sp.Einv;
     if (!apply_einv) {
         out = g;
         return OV_OK;
@@ -1359,7 +1368,7 @@ int dspace_coeffs(ov_ctx* c, DefSpace& sp, const void* A, const void* v, std::ve
     for (int i = 0; i < n; ++i) {
         double re = 0.0, im = 0.0;
         for (int k = 0; k < n; ++k) {
-            const HostCplx e = sp.Einv[i + (size_t)k * n], x = g[k];
+            const HostCplx e = Einv[i + (size_t)k * n], x = g[k];
             re += e.re * x.re - e.im * x.im;
             im += e.re * x.im + e.im * x.re;
         }
@@ -1617,17 +1626,19 @@ int dspace_fp64(ov_ctx* c, DefSpace& sp, cudaStream_t s) {
 }
 
 // CG on the chiral-sector normal operator A_s = P_s [2 (1 - m^2/4)(1 + s sign) + m^2] P_s for each
-// system (rhs vector B_k in sector chi_k), in precision R.  Y: solutions, in the order of S.
+// system (rhs vector B_k in sector chi_k), in precision R (ST: storage of the polynomial loop's
+// links and vectors, R or a 16-bit format with R = float).  Y: solutions, in the order of S.
 // Converged systems leave the batch: the active ones are kept at the front (a converged
 // system is swapped with the last active one), so later sign applications run only on
 // systems that still iterate; Y is put back in the original order at the end.
-template <typename R>
-// coef0 (optional): for each system whose space carries the FP64 part, the Galerkin start is
+// coef0 (optional, FP32): for each system whose space carries the FP64 part, the Galerkin start is
 // returned as coefficients c (y = W c + Y) instead of being added to Y in FP32: its size, about
 // |r| / lambda_min, would leave FP32 rounding of that order in Y.
+template <typename R, typename ST = R>
 int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, const std::vector<double>& tol_rel0,
              int max_iter, int* iters, cudaStream_t s, int degree = 0,
              std::vector<std::vector<HostCplx>>* coef0 = nullptr) {
+    constexpr bool F64 = std::is_same<R, double>::value;
     const int prec = prec_of<R>();
     const int ns = S0.n;
     const long long n12 = 12LL * c->g.V;
@@ -1650,30 +1661,36 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
     std::vector<double2> pap(ns);
     norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
     b2 = rr;
-    // Deflation with the D_ov low modes of each system's (phase, chirality) (FP32): start from the
-    // Galerkin solution on the space, y = W E^-1 W^+ b (E = W^+ A W), and keep the search
-    // directions A-orthogonal to it, p = r + beta p - W E^-1 (A W)^+ r (deflated CG).
+    // Deflation with the D_ov low modes of each system's (phase, chirality), in the CG's precision
+    // (FP32 vectors, or their FP64 counterparts W, A(m) W for an FP64 CG): start from the Galerkin
+    // solution on the space, y = W E^-1 W^+ b (E = W^+ A W), and keep the search directions
+    // A-orthogonal to it, p = r + beta p - W E^-1 (A W)^+ r (deflated CG).
     std::vector<DefSpace*> dsp(ns, nullptr);
     bool any_defl = false;
-    if constexpr (std::is_same<R, float>::value) {
-        for (int k = 0; k < ns; ++k) {
-            DefSpace* sp = S0.chi.empty() ? nullptr : find_dspace(c, S0.phase[k], S0.chi[k]);
-            if (!sp || !(rr[k] > 0.0)) continue;
+    auto Wof = [](DefSpace* sp) -> const void* { return F64 ? sp->W64 : sp->W; };
+    auto AWof = [](DefSpace* sp) -> const void* { return F64 ? sp->AWm64 : sp->AWm; };
+    for (int k = 0; k < ns; ++k) {
+        DefSpace* sp = S0.chi.empty() ? nullptr : find_dspace(c, S0.phase[k], S0.chi[k]);
+        if (!sp || !(rr[k] > 0.0)) continue;
+        if (F64) {
+            if (!sp->AW64) continue;  // no FP64 data for this space
+            TRY(dspace_prepare64(c, *sp, mass, s));
+        } else {
             TRY(dspace_prepare(c, *sp, mass, s));
-            char* bk = (char*)B + (size_t)k * vb;
-            char* rk = (char*)r + (size_t)k * vb;
-            std::vector<HostCplx> dco, mu;
-            TRY(dspace_coeffs(c, *sp, sp->W, bk, dco, true, s));
-            if (coef0 && sp->DW64) (*coef0)[k] = dco;  // kept in FP64 by the caller
-            else TRY(dspace_combine(c, sp->W, sp->n, dco, 1.0, nullptr, (char*)Y + (size_t)k * vb, s));
-            TRY(dspace_combine(c, sp->AWm, sp->n, dco, -1.0, bk, rk, s));
-            TRY(dspace_coeffs(c, *sp, sp->AWm, rk, mu, true, s));
-            TRY(dspace_combine(c, sp->W, sp->n, mu, -1.0, rk, (char*)p + (size_t)k * vb, s));
-            dsp[k] = sp;
-            any_defl = true;
         }
-        if (any_defl) norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
+        char* bk = (char*)B + (size_t)k * vb;
+        char* rk = (char*)r + (size_t)k * vb;
+        std::vector<HostCplx> dco, mu;
+        TRY(dspace_coeffs<R>(c, *sp, Wof(sp), bk, dco, true, s));
+        if (!F64 && coef0 && sp->DW64) (*coef0)[k] = dco;  // kept in FP64 by the caller
+        else TRY(dspace_combine<R>(c, Wof(sp), sp->n, dco, 1.0, nullptr, (char*)Y + (size_t)k * vb, s));
+        TRY(dspace_combine<R>(c, AWof(sp), sp->n, dco, -1.0, bk, rk, s));
+        TRY(dspace_coeffs<R>(c, *sp, AWof(sp), rk, mu, true, s));
+        TRY(dspace_combine<R>(c, Wof(sp), sp->n, mu, -1.0, rk, (char*)p + (size_t)k * vb, s));
+        dsp[k] = sp;
+        any_defl = true;
     }
+    if (any_defl) norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
     auto swap_vec = [&](void* base, int i, int j) -> int {
         char* bi = (char*)base + (size_t)i * vb;
         char* bj = (char*)base + (size_t)j * vb;
@@ -1716,7 +1733,7 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
         A.n = na;
         A.phase.assign(S.phase.begin(), S.phase.begin() + na);
         A.chi.assign(S.chi.begin(), S.chi.begin() + na);
-        TRY(sign_pipeline<R>(c, p, A, false, fin, Ap, s, degree));
+        TRY((sign_pipeline<R, ST>(c, p, A, false, fin, Ap, s, degree)));
         dot_rhs<R>(p, Ap, n12, na, pap.data(), c->d_partial, c->d_red, s);
         for (int k = 0; k < na; ++k) {
             if (!std::isfinite(pap[k].x) || !std::isfinite(rr[k]))
@@ -1742,9 +1759,9 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
                 const void* dir = rk;
                 if (dsp[k]) {  // r - W E^-1 (A W)^+ r
                     std::vector<HostCplx> mu;
-                    TRY(dspace_coeffs(c, *dsp[k], dsp[k]->AWm, rk, mu, true, s));
+                    TRY(dspace_coeffs<R>(c, *dsp[k], AWof(dsp[k]), rk, mu, true, s));
                     char* tk = (char*)tmp + (size_t)k * vb;
-                    TRY(dspace_combine(c, dsp[k]->W, dsp[k]->n, mu, -1.0, rk, tk, s));
+                    TRY(dspace_combine<R>(c, Wof(dsp[k]), dsp[k]->n, mu, -1.0, rk, tk, s));
                     dir = tk;
                 }
                 launch_axpby<R>(&ones[k], dir, &beta[k], pk, n12, 1, s);
@@ -1779,7 +1796,7 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
 // number of masses.  Z is [mass][system]; Z[i][k] returns A(m_i)^{-1} B_k (the factor k_b / k_i
 // applied).  A shift whose residual |zeta_i| |r| meets its system's tolerance stops updating; a
 // system leaves the batch when its seed (the lightest mass, the last to converge) does.
-template <typename R>
+template <typename R, typename ST = R>
 int inner_cg_shifted(ov_ctx* c, const std::vector<double>& mass, const SysSet& S0, const void* B, void* Z,
                      const std::vector<double>& tol_rel0, int max_iter, int* iters, cudaStream_t s, int degree) {
     const int prec = prec_of<R>();
@@ -1869,7 +1886,7 @@ int inner_cg_shifted(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
         A.chi.assign(S.chi.begin(), S.chi.begin() + na);
         void* pb = at(P, ib, 0);
         fin.v2 = pb;
-        TRY(sign_pipeline<R>(c, pb, A, false, fin, Ap, s, degree));  // Ap = M p (seed direction)
+        TRY((sign_pipeline<R, ST>(c, pb, A, false, fin, Ap, s, degree)));  // Ap = M p (seed direction)
         dot_rhs<R>(pb, Ap, n12, na, pap.data(), c->d_partial, c->d_red, s);
         for (int k = 0; k < na; ++k) {
             if (!std::isfinite(pap[k].x) || !std::isfinite(rr[k]))
@@ -1952,7 +1969,9 @@ int inner_cg_shifted(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
     return na > 0 ? OV_ERR_NOT_CONVERGED : OV_OK;
 }
 
-template <typename R>
+// R: arithmetic of the inner CG and its correction (FP64 or FP32); ST: storage of their polynomial
+// loops (R, or FP16 / BF16 with R = float).  The true residual and x stay FP64.
+template <typename R, typename ST = R>
 int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* x, double tol, ov_solve_stats* st,
                cudaStream_t s) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -2100,7 +2119,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         }
         int iters = 0;
         std::vector<std::vector<HostCplx>> coef0(ns);
-        int rc = inner_cg<R>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s, degree, &coef0);
+        int rc = inner_cg<R, ST>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s, degree, &coef0);
         for (int k = 0; k < ns; ++k) {
             if (c_low[k].empty()) continue;
             if (coef0[k].empty()) coef0[k].assign(c_low[k].size(), HostCplx{0, 0});
@@ -2123,7 +2142,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             count_launch();
             CKL();
         }
-        TRY(overlap_op<R>(c, Ysum, Srhs, mass, true, E, s, degree));
+        TRY((overlap_op<R, ST>(c, Ysum, Srhs, mass, true, E, s, degree)));
         if (std::is_same<R, double>::value)
             CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
         else
@@ -2181,7 +2200,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
 // multi-shift CG over the chiral sectors of b (undeflated: a shared Krylov space cannot carry a
 // per-mass deflation) gives y_i for all masses, and x_i = D(m_i)^+ y_i.  Each mass then finishes
 // in solve_impl from x_i (FP64 true residual, deflated cycles).  x: [mass][rhs] ABI spinors.
-template <typename R>
+template <typename R, typename ST = R>
 int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& Srhs, const void* b, void* x,
                      double tol, ov_solve_stats* st, cudaStream_t s) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -2254,7 +2273,7 @@ int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
             for (double m : mass) mmin = std::min(mmin, std::fabs(m));
             degree = degree_for_delta(c, 0.5 * mmin * g);
         }
-        rc = inner_cg_shifted<R>(c, mass, S, Bs, Z, tol_rel, c->p.max_iter, &iters, s, degree);
+        rc = inner_cg_shifted<R, ST>(c, mass, S, Bs, Z, tol_rel, c->p.max_iter, &iters, s, degree);
         if (rc != OV_OK && rc != OV_ERR_NOT_CONVERGED) return rc;
     }
     // x_i = D(m_i)^+ (y_{i,+} + y_{i,-})
@@ -2270,7 +2289,7 @@ int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
                                                 (typename C2<R>::T*)Ysum, n12);
         count_launch();
         CKL();
-        TRY(overlap_op<R>(c, Ysum, Srhs, mass[i], true, E, s, degree));
+        TRY((overlap_op<R, ST>(c, Ysum, Srhs, mass[i], true, E, s, degree)));
         if (std::is_same<R, double>::value)
             CK(cudaMemcpyAsync(E64, E, vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
         else
@@ -2288,7 +2307,7 @@ int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
     int status = OV_OK;
     for (int i = 0; i < nm; ++i) {
         ov_solve_stats sti{};
-        const int rci = solve_impl<R>(c, mass[i], Srhs, b, (char*)x + (size_t)i * abi_bytes, tol, &sti, s);
+        const int rci = solve_impl<R, ST>(c, mass[i], Srhs, b, (char*)x + (size_t)i * abi_bytes, tol, &sti, s);
         snprintf(buf, sizeof(buf), " || m %g: ", mass[i]);
         info += buf + c->info;
         if (st) {
@@ -2310,6 +2329,16 @@ int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
     return status;
 }
 
+int solve_dispatch(ov_ctx* c, double mass, const SysSet& S, const void* b, void* x, double tol, ov_solve_stats* st,
+                   cudaStream_t s) {
+    switch (c->p.inner_precision) {
+        case OV_PREC_F64: return solve_impl<double>(c, mass, S, b, x, tol, st, s);
+        case OV_PREC_F32: return solve_impl<float>(c, mass, S, b, x, tol, st, s);
+        case OV_PREC_F16: return solve_impl<float, H16>(c, mass, S, b, x, tol, st, s);
+        default: return solve_impl<float, B16>(c, mass, S, b, x, tol, st, s);
+    }
+}
+
 }  // namespace
 
 extern "C" int solve_overlap_multimass(ov_ctx* c, int n_mass, const double* masses, const double* phase, const void* b,
@@ -2326,8 +2355,12 @@ extern "C" int solve_overlap_multimass(ov_ctx* c, int n_mass, const double* mass
     SysSet S = make_sys(nrhs, phase);
     TRY(phase_check(c, S));
     cudaStream_t s = (cudaStream_t)stream;
-    return c->p.inner_precision == OV_PREC_F64 ? solve_multi_impl<double>(c, m, S, b, x, tol, stats, s)
-                                               : solve_multi_impl<float>(c, m, S, b, x, tol, stats, s);
+    switch (c->p.inner_precision) {
+        case OV_PREC_F64: return solve_multi_impl<double>(c, m, S, b, x, tol, stats, s);
+        case OV_PREC_F32: return solve_multi_impl<float>(c, m, S, b, x, tol, stats, s);
+        case OV_PREC_F16: return solve_multi_impl<float, H16>(c, m, S, b, x, tol, stats, s);
+        default: return solve_multi_impl<float, B16>(c, m, S, b, x, tol, stats, s);
+    }
 }
 
 extern "C" int solve_overlap(ov_ctx* c, double mass, const double* phase, const void* b, void* x, int nrhs, double tol,
@@ -2337,8 +2370,14 @@ extern "C" int solve_overlap(ov_ctx* c, double mass, const double* phase, const 
     SysSet S = make_sys(nrhs, phase);
     TRY(phase_check(c, S));
     cudaStream_t s = (cudaStream_t)stream;
-    return c->p.inner_precision == OV_PREC_F64 ? solve_impl<double>(c, mass, S, b, x, tol, stats, s)
-                                               : solve_impl<float>(c, mass, S, b, x, tol, stats, s);
+    return solve_dispatch(c, mass, S, b, x, tol, stats, s);
+}
+
+extern "C" int ov_set_inner_precision(ov_ctx* c, int inner_precision) {
+    if (!c) return OV_ERR_ARG;
+    TRY(check_inner_precision(c, &c->p, inner_precision));
+    c->p.inner_precision = inner_precision;
+    return OV_OK;
 }
 
 extern "C" int ov_eigensolve_overlap(ov_ctx* c, double phase, int chirality, int n_ev, int krylov, double tol,
@@ -2775,8 +2814,7 @@ int ov_dcorr_dE(ov_ctx* c, double mass, double charge, double E, const void* S, 
         TRY(workspace(c, "dc_W", OV_PREC_F64, nrhs, &Wsol));
         CK(cudaMemsetAsync(Wsol, 0, vec_bytes(c, OV_PREC_F64) * nrhs, s));
         ov_solve_stats st{};
-        const int rc = c->p.inner_precision == OV_PREC_F64 ? solve_impl<double>(c, mass, Sph, U, Wsol, tol, &st, s)
-                                                           : solve_impl<float>(c, mass, Sph, U, Wsol, tol, &st, s);
+        const int rc = solve_dispatch(c, mass, Sph, U, Wsol, tol, &st, s);
         if (rc != OV_OK) return rc;
         left = S;
         right = Wsol;

@@ -115,3 +115,36 @@ def test_deflated_solve_matches_oracle(P, lat, mass, phase, adaptive):
         r = b[j] - ov.overlap(d["U"], xs[True][j], mass, p, small, phase)
         assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol
     assert iters[True] < iters[False]
+
+
+@pytest.mark.parametrize("inner", ["f64", "f16", "bf16"])
+def test_deflated_solve_in_other_inner_precisions(P, lat, inner):
+    """The same deflated, adaptive-order solve with an FP64 inner CG (deflated with the spaces' FP64
+    vectors) and with FP16 / BF16 storage of the inner CG's polynomial loops (FP32 arithmetic): each
+    must reach the tolerance against the oracle's operator; the 16-bit ones take more outer cycles."""
+    import torch
+
+    d, tol, mass, phase = lat, 1e-10, 0.02, 0.2
+    prec = {"f64": 0, "f16": 2, "bf16": 3}[inner]
+    ctx = P.Context(P.Params(dims=d["dims"], bc=d["bc"], m0=M0, eps=EPS4, poly_degree=DEGREE,
+                             precision=1 if inner == "f64" else prec, inner_precision=1, max_nrhs=4,
+                             adaptive_order=1))
+    ctx.set_gauge(dev(d["U"]))
+    for ph, (lam, V) in d["banks"].items():
+        P.deflate(ctx, dev(V), lam, phase=ph)
+    for chi in (1, -1):
+        P.eigensolve_overlap(ctx, 16, chirality=chi, phase=phase)
+    ctx.set_inner_precision(prec)
+    b = synth.point_sources(d["dims"], [(0, 1), (3, 2)])
+    xd = torch.zeros_like(dev(b))
+    st = P.solve_overlap(ctx, dev(b), xd, mass, tol=tol, phase=[phase, phase])
+    print(f"inner {inner}: outer {st.outer_iters}, inner {st.inner_iters}: {ctx.last_info}")
+    assert st.true_residual <= tol
+    x = xd.cpu().numpy()
+    lam, V = d["banks"][phase]
+    small = ov.SmallSpace.from_eigenpairs(V, lam)
+    p = ov.OverlapParams(m0=M0, hw_norm=HW, eps=EPS4, degree=DEGREE, bc=(1.0, 1.0, 1.0, -1.0))
+    for j in range(2):
+        r = b[j] - ov.overlap(d["U"], x[j], mass, p, small, phase)
+        assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol
+    ctx.close()

@@ -95,7 +95,17 @@ def test_create_rejects_invalid_parameters(ovl, bad):
 def test_create_accepts_16bit_storage(ovl, precision):
     ctx = ovl.Context(ovl.Params(dims=(4, 4, 4, 4), precision=precision, inner_precision=1))
     assert ctx.spinor_dtype() == __import__("torch").complex64
+    # the solver may use the context's own 16-bit format, not the other one
+    ctx.set_inner_precision(precision)
+    other = ovl.OV_PREC_BF16 if precision == ovl.OV_PREC_F16 else ovl.OV_PREC_F16
+    with pytest.raises(ovl.OvlError) as e:
+        ctx.set_inner_precision(other)
+    assert e.value.code == ovl.OV_ERR_ARG
+    ctx.set_inner_precision(ovl.OV_PREC_F64)
     ctx.close()
+    ovl.Context(ovl.Params(dims=(4, 4, 4, 4), precision=precision, inner_precision=precision)).close()
+    with pytest.raises(ovl.OvlError):
+        ovl.Context(ovl.Params(dims=(4, 4, 4, 4), precision=ovl.OV_PREC_F32, inner_precision=precision))
 
 
 @pytest.mark.parametrize("shape", [1, 2 | 16, 4 | 8 | 16])
