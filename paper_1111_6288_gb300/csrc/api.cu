@@ -116,6 +116,7 @@ struct ov_ctx {
     int cap_sys = 0;
     long long dslash_count = 0;
     long long sign_count = 0;
+    long long cg_stalls = 0;  // inner-CG systems stopped at a stalled residual (16-bit storage)
     // optional CUDA-event timing of the Clenshaw loops (the Wilson kernels of the polynomial)
     // CUDA graphs of the Clenshaw loop, keyed by precision, systems and buffers
     bool use_graphs = true;
@@ -1659,6 +1660,14 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
     std::iota(perm.begin(), perm.end(), 0);
     std::vector<double> rr(ns), rr_new(ns), b2(ns), alpha(ns), beta(ns), ones(ns, 1.0);
     std::vector<double2> pap(ns);
+    // 16-bit storage: the operator carries rounding of ~1e-3 that differs between applications, so
+    // the CG residual stalls near that level; a system whose best residual has not halved within
+    // kStall iterations leaves the batch (the outer FP64 loop continues from its iterate)
+    constexpr bool HALF = !std::is_same<R, ST>::value;
+    constexpr int kStall = 100;
+    std::vector<double> best(ns, 0.0);
+    std::vector<int> best_it(ns, 0);
+    int stalled = 0;
     norm2_rhs<R>(r, n12, ns, rr.data(), c->d_partial, c->d_red, s);
     b2 = rr;
     // Deflation with the D_ov low modes of each system's (phase, chirality), in the CG's precision
@@ -1713,6 +1722,8 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
             std::swap(S.phase[k], S.phase[last]);
             std::swap(S.chi[k], S.chi[last]);
             std::swap(dsp[k], dsp[last]);
+            std::swap(best[k], best[last]);
+            std::swap(best_it[k], best_it[last]);
         }
         --na;
         return OV_OK;
@@ -1768,10 +1779,24 @@ int inner_cg(ov_ctx* c, double mass, const SysSet& S0, const void* B, void* Y, c
             }
         }
         CKL();
-        for (int k = na - 1; k >= 0; --k)
-            if (std::sqrt(rr[k]) <= tol_rel[k] * std::sqrt(b2[k])) TRY(retire(k, na));
+        for (int k = na - 1; k >= 0; --k) {
+            if (std::sqrt(rr[k]) <= tol_rel[k] * std::sqrt(b2[k])) {
+                TRY(retire(k, na));
+                continue;
+            }
+            if (HALF) {
+                if (best[k] == 0.0 || rr[k] < 0.25 * best[k]) {  // |r| halved: a new reference point
+                    best[k] = rr[k];
+                    best_it[k] = it;
+                } else if (it - best_it[k] >= kStall) {
+                    ++stalled;
+                    TRY(retire(k, na));
+                }
+            }
+        }
     }
     *iters = it;
+    if (stalled) c->cg_stalls += stalled;
     // back to the original order: position k holds system perm[k]
     bool moved = false;
     for (int k = 0; k < ns; ++k) moved = moved || perm[k] != k;
@@ -1969,6 +1994,18 @@ int inner_cg_shifted(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
     return na > 0 ? OV_ERR_NOT_CONVERGED : OV_OK;
 }
 
+// Relative tolerance of an inner solve when the caller set none: FP64 the outer target itself, FP32
+// 1e-6, and above the operator's own rounding for the 16-bit formats (FP16 1e-2, BF16 3e-2: one sign
+// application carries ~2e-3 / ~1e-2 relative error at these degrees).
+template <typename R, typename ST>
+double inner_base_tol(const ov_ctx* c) {
+    if (c->p.inner_tol > 0.0) return c->p.inner_tol;
+    if (std::is_same<R, double>::value) return 0.0;
+    if (std::is_same<ST, H16>::value) return 1e-2;
+    if (std::is_same<ST, B16>::value) return 3e-2;
+    return 1e-6;
+}
+
 // R: arithmetic of the inner CG and its correction (FP64 or FP32); ST: storage of their polynomial
 // loops (R, or FP16 / BF16 with R = float).  The true residual and x stay FP64.
 template <typename R, typename ST = R>
@@ -2023,7 +2060,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
     } else {
         TRY(true_residual());
     }
-    const double base_tol = c->p.inner_tol > 0.0 ? c->p.inner_tol : (prec == OV_PREC_F64 ? 0.0 : 1e-6);
+    const double base_tol = inner_base_tol<R, ST>(c);
     int outer = 0, inner_total = 0, status = OV_OK;
     std::string hist = "solve:";
     const int max_outer = 60;
@@ -2118,6 +2155,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             degree = degree_for_delta(c, 0.5 * std::fabs(mass) * g);
         }
         int iters = 0;
+        const long long stalls0 = c->cg_stalls;
         std::vector<std::vector<HostCplx>> coef0(ns);
         int rc = inner_cg<R, ST>(c, mass, S, Bs, Ys, tol_rel, c->p.max_iter - inner_total, &iters, s, degree, &coef0);
         for (int k = 0; k < ns; ++k) {
@@ -2166,8 +2204,9 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
             double worst = 0.0;
             for (int j = 0; j < nrhs; ++j) worst = std::max(worst, res[j]);
             char buf[128];
-            snprintf(buf, sizeof(buf), " | cycle %d: n %d, %d inner, %d systems, residual %.2e", outer,
-                     degree > 0 ? degree : c->p.poly_degree, iters, ns, worst);
+            snprintf(buf, sizeof(buf), " | cycle %d: n %d, %d inner, %d systems%s, residual %.2e", outer,
+                     degree > 0 ? degree : c->p.poly_degree, iters, ns,
+                     c->cg_stalls > stalls0 ? " (stalled)" : "", worst);
             hist += buf;
         }
     }
@@ -2245,7 +2284,7 @@ int solve_multi_impl(ov_ctx* c, const std::vector<double>& mass, const SysSet& S
         CKL();
         std::vector<double> sn2(ns0);
         norm2_rhs<double>(S64, n12, ns0, sn2.data(), c->d_partial, c->d_red, s);
-        const double base_tol = c->p.inner_tol > 0.0 ? c->p.inner_tol : (prec == OV_PREC_F64 ? 0.0 : 1e-6);
+        const double base_tol = inner_base_tol<R, ST>(c);
         for (int k = 0; k < ns0; ++k) {
             const int j = src[k];
             if (!(sn2[k] > 0.0) || std::sqrt(sn2[k]) <= 0.25 * tol * std::sqrt(bn2[j])) continue;
