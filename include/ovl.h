@@ -275,6 +275,21 @@ int deflate(ov_ctx* ctx, double phase, const void* V, const double* lambda, int 
 int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_iter,
                     void* V_out, double* lambda_out, int register_bank, ov_stream_t stream);
 
+/* The small-space projection alone (Sec. 2, Fig. 1: the exactly treated low modes), as apply_sign_Hw
+ * applies it: with the bank V, s registered for `phase` by deflate(),
+ *   xperp = in - V (V^+ in),   ys = V diag(s) (V^+ in)
+ * (an empty small space for phase 0 without a bank: xperp = in, ys = 0; OV_ERR_NO_BANK for another
+ * phase without one).  in, ys, xperp: device [nrhs][site][4][3], complex128 in an FP64 context,
+ * complex64 otherwise (FP32 arithmetic on the FP32 copy of the bank), three different buffers. */
+int ov_project_small(ov_ctx* ctx, double phase, const void* in, void* ys, void* xperp, int nrhs,
+                     ov_stream_t stream);
+
+/* How FP32 projections of 8 or more vectors run: 0 = on the faster of the two paths, timed once per
+ * (bank size, batch size) on the call's own buffers (ov_tune_info lists the times); 1 = CUDA cores;
+ * 2 = tensor cores (tcgen05, TF32 with a three-term split for FP32 accuracy; bank size <= 384).
+ * FP64 projections and batches below 8 always use the CUDA cores.  Default 0. */
+int ov_set_projection(ov_ctx* ctx, int method);
+
 /* ---- propagator solve (Sec. 3.2) --------------------------------------- */
 
 /* Solve D(m) x = b for nrhs right-hand sides to ||b - D(m) x|| / ||b|| <= tol, with D(m)

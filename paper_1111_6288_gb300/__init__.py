@@ -55,6 +55,7 @@ from ._ovl import (  # noqa: F401
     library_path,
     pion_correlator,
     poly_delta,
+    project_small,
     selftest_bounded_wait,
     solve_overlap,
     solve_overlap_multimass,

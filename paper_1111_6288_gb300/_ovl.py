@@ -97,6 +97,8 @@ _SIGNATURES = {
     "apply_sign_Hw": (_I, [_VP, _VP, _VP, _I, _DP, _VP]),
     "apply_overlap": (_I, [_VP, _VP, _VP, _I, _D, _DP, _VP]),
     "apply_wilson_noalloc": (_I, [C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _VP, _VP, _VP, _I, _DP, _I, _VP]),
+    "ov_project_small": (_I, [_VP, _D, _VP, _VP, _VP, _I, _VP]),
+    "ov_set_projection": (_I, [_VP, _I]),
     "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
     "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
     "ov_set_inner_precision": (_I, [_VP, _I]),
@@ -280,6 +282,10 @@ class Context:
         _check(lib().ov_set_inner_precision(self.handle, int(precision)), self.handle)
         self.params.inner_precision = int(precision)
 
+    def set_projection(self, method):
+        """FP32 small-space projections of 8+ vectors: 0 timed choice, 1 CUDA cores, 2 tensor cores."""
+        _check(lib().ov_set_projection(self.handle, int(method)), self.handle)
+
     def set_profiling(self, on=True):
         """Record CUDA events around every polynomial (Clenshaw) loop."""
         _check(lib().ov_set_profiling(self.handle, int(on)), self.handle)
@@ -371,6 +377,16 @@ def apply_overlap(ctx: Context, x, out, mass=0.0, phase=None, stream=None):
     _check(lib().apply_overlap(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, float(mass), ph,
                                _stream(stream)), ctx.handle)
     return out
+
+
+def project_small(ctx: Context, x, ys, xperp, phase=0.0, stream=None):
+    """ys = V diag(s) V^+ x and xperp = x - V V^+ x with the bank registered for phase."""
+    n = ctx._check_spinor(x, "x")
+    ctx._check_spinor(ys, "ys")
+    ctx._check_spinor(xperp, "xperp")
+    _check(lib().ov_project_small(ctx.handle, float(phase), C.c_void_p(x.data_ptr()), C.c_void_p(ys.data_ptr()),
+                                  C.c_void_p(xperp.data_ptr()), n, _stream(stream)), ctx.handle)
+    return ys, xperp
 
 
 def deflate(ctx: Context, V, lam, phase=0.0, stream=None):

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libovl.so")
-SOURCES = ["dslash.cu", "blas.cu", "api.cu", "noalloc.cu", "hostla.cpp"]
+SOURCES = ["dslash.cu", "blas.cu", "api.cu", "noalloc.cu", "proj_tc.cu", "hostla.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -122,6 +122,11 @@ struct ov_ctx {
     bool use_graphs = true;
     // autotuned right-hand sides per Wilson-kernel block, keyed by precision and systems
     std::map<std::pair<int, int>, int> launch_shape;
+    // small-space projection of FP32 vectors: 0 = timed per (bank size, batch), 1 = CUDA cores,
+    // 2 = tensor cores; the timed choice per (bank size, batch)
+    int proj_method = 0;
+    std::map<std::pair<int, int>, int> proj_choice;
+    Buf tc_img;  // pre-split coefficients of the tensor-core projection
     std::string tune_log;
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, std::pair<cudaGraphExec_t, void*>> graphs;  // exec, buffer holding p
@@ -418,6 +423,83 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
     return best;
 }
 
+int take_timeouts() {
+    const int a = take_wait_timeouts(), b = take_tc_timeouts();
+    if (a < 0 || b < 0) return -1;
+    return a | b;
+}
+
+// Batches of at least this many FP32 vectors may take the tensor-core projection.
+constexpr int kTcMinBatch = 8;
+
+// The small-space projection of k vectors (precision R, internal layout) on the bank b:
+// C = V^+ X, Xp = X - V C, Ys = V diag(s) C.  FP32 batches of kTcMinBatch or more vectors go through
+// the tcgen05 kernels when the context's method says so, or, by default, when they measured faster for
+// this (bank size, batch) the first time it appeared (both paths timed on the call's own buffers).
+template <typename R>
+int project_bank(ov_ctx* c, const Bank* b, const void* X, int k, void* Xp, void* Ys, cudaStream_t s) {
+    const int N = b->n;
+    const long long n12 = 12LL * c->g.V;
+    const void* Vb = std::is_same<R, double>::value ? b->V64 : b->V32;
+    TRY(ensure_small(c, 2LL * N * k, std::max<long long>((long long)N * 4 * 4 * 152, 152LL * N * std::min(k, 32)),
+                     std::max(k, 1)));
+    int method = 1;
+    if (std::is_same<R, float>::value && k >= kTcMinBatch && N <= kTcMaxBank && tc_project_available())
+        method = c->proj_method;
+    if (method == 1) {
+        small_space_project<R>(Vb, N, b->d_signs, X, k, Xp, Ys, n12, c->d_C, c->d_partial, c->partial_cap, s);
+        CKL();
+        return OV_OK;
+    }
+    const size_t img = tc_project_image_bytes(N);
+    if (c->tc_img.bytes < img) {
+        if (c->tc_img.ptr) {
+            CK(cudaDeviceSynchronize());
+            CK(cudaFree(c->tc_img.ptr));
+            c->tc_img.ptr = nullptr;
+            c->tc_img.bytes = 0;
+        }
+        CK(cudaMalloc(&c->tc_img.ptr, img));
+        c->tc_img.bytes = img;
+    }
+    auto run = [&](int m) -> cudaError_t {
+        if (m == 2)
+            return small_space_project_tc(Vb, N, b->d_signs, X, k, Xp, Ys, n12, c->d_C, c->d_partial, c->partial_cap,
+                                          c->tc_img.ptr, s);
+        small_space_project<R>(Vb, N, b->d_signs, X, k, Xp, Ys, n12, c->d_C, c->d_partial, c->partial_cap, s);
+        return cudaGetLastError();
+    };
+    if (method == 0) {
+        const auto key = std::make_pair(N, k);
+        auto it = c->proj_choice.find(key);
+        if (it == c->proj_choice.end()) {
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            float ms[3] = {0.f, 0.f, 0.f};
+            for (int m : {1, 2}) {
+                CK(run(m));  // warm
+                CK(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r) CK(run(m));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(&ms[m], e0, e1));
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            const int best = ms[2] < ms[1] ? 2 : 1;
+            char buf[128];
+            snprintf(buf, sizeof(buf), "projection N %d k %d: cuda cores %.1fus tensor cores %.1fus; ", N, k,
+                     1e3f * ms[1] / 3, 1e3f * ms[2] / 3);
+            c->tune_log += buf;
+            it = c->proj_choice.emplace(key, best).first;
+        }
+        method = it->second;
+    }
+    CK(run(method));
+    return OV_OK;
+}
+
 // out = Proj(G(c_op H_w P(Q^2) x_perp + c1 y_s)) + c2 v2 + c3 v3 over S.n systems of precision R,
 // where (y_s, x_perp) is the projection of (g5_in ? gamma5 X : X).  fin.v1 is set here.
 // ST: storage of the links and vectors of the recurrence: R itself, or (R = float) a 16-bit
@@ -475,12 +557,8 @@ int sign_pipeline(ov_ctx* c, const void* X, const SysSet& S, bool g5_in, Epilogu
             CK(cudaMemsetAsync(ys_j, 0, (size_t)k * n12 * es, s));
         } else {
             any_bank = true;
-            const int N = b->n;
-            const void* Vb = std::is_same<R, double>::value ? b->V64 : b->V32;
-            TRY(ensure_small(c, 2LL * N * k, (long long)N * 4 * 4 * 152, ns));
-            small_space_project<R>(Vb, N, b->d_signs, src_j, k, xp_j, ys_j, n12, c->d_C, c->d_partial,
-                                   c->partial_cap, s);
-            CKL();
+            TRY(ensure_small(c, 0, 0, ns));
+            TRY(project_bank<R>(c, b, src_j, k, xp_j, ys_j, s));
         }
         j0 = j1;
     }
@@ -970,6 +1048,7 @@ int ov_destroy(ov_ctx* c) {
     for (auto& sp : c->dspaces)
         for (void* q : {sp.W, sp.AW0, sp.AWm, sp.W64, sp.DW64, sp.DmW64, sp.AW64, sp.AWm64})
             if (q) cudaFree(q);
+    if (c->tc_img.ptr) cudaFree(c->tc_img.ptr);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& v : c->prof_events)
@@ -1000,7 +1079,7 @@ int ov_selftest_bounded_wait(ov_ctx* c, ov_stream_t stream) {
 int ov_sync(ov_ctx* c, ov_stream_t stream) {
     if (!c) return OV_ERR_ARG;
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    const int t = take_wait_timeouts();
+    const int t = take_timeouts();
     if (t < 0) return fail(c, OV_ERR_CUDA, "reading the device wait flag failed");
     if (t > 0) return fail(c, OV_ERR_TIMEOUT, "a bounded device wait ran out");
     return OV_OK;
@@ -1120,6 +1199,54 @@ int apply_overlap(ov_ctx* c, const void* in, void* out, int nrhs, double mass, c
     if (!std::isfinite(mass)) return fail(c, OV_ERR_ARG, "mass not finite");
     cudaStream_t s = (cudaStream_t)stream;
     return apply_dispatch(c, in, out, nrhs, phase, 3, mass, s);
+}
+
+int ov_set_projection(ov_ctx* c, int method) {
+    if (!c) return OV_ERR_ARG;
+    if (method < 0 || method > 2) return fail(c, OV_ERR_ARG, "projection method = %d invalid", method);
+    if (method == 2 && !tc_project_available())
+        return fail(c, OV_ERR_ARG, "tensor-core projection unavailable (no tensor-map encoder in the driver)");
+    c->proj_method = method;
+    return OV_OK;
+}
+
+int ov_project_small(ov_ctx* c, double phase, const void* in, void* ys, void* xperp, int nrhs, ov_stream_t stream) {
+    if (!c) return OV_ERR_ARG;
+    if (!in || !ys || !xperp) return fail(c, OV_ERR_ARG, "null spinor pointer");
+    if (in == ys || in == xperp || ys == xperp) return fail(c, OV_ERR_ARG, "in, ys and xperp must be different buffers");
+    if (nrhs < 1 || nrhs > c->p.max_nrhs)
+        return fail(c, OV_ERR_ARG, "nrhs = %d outside [1, max_nrhs = %d]", nrhs, c->p.max_nrhs);
+    if (!std::isfinite(phase)) return fail(c, OV_ERR_ARG, "non-finite phase");
+    Bank* b = find_bank(c, phase);
+    if (!b && phase != 0.0) return fail(c, OV_ERR_NO_BANK, "no small-space bank registered for phase %.17g", phase);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool f64 = c->p.precision == OV_PREC_F64;
+    const int prec = f64 ? OV_PREC_F64 : OV_PREC_F32, dt = f64 ? OV_C128 : OV_C64;
+    void *X, *P, *Y;
+    TRY(workspace(c, "pj_in", prec, nrhs, &X));
+    TRY(workspace(c, "pj_xp", prec, nrhs, &P));
+    TRY(workspace(c, "pj_ys", prec, nrhs, &Y));
+    const size_t bytes = vec_bytes(c, prec) * nrhs;
+    if (f64) launch_pack_spinor<double>(in, dt, X, c->g.V, nrhs, s);
+    else launch_pack_spinor<float>(in, dt, X, c->g.V, nrhs, s);
+    CKL();
+    if (!b || b->n == 0) {
+        CK(cudaMemcpyAsync(P, X, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(Y, 0, bytes, s));
+    } else if (f64) {
+        TRY(project_bank<double>(c, b, X, nrhs, P, Y, s));
+    } else {
+        TRY(project_bank<float>(c, b, X, nrhs, P, Y, s));
+    }
+    if (f64) {
+        launch_unpack_spinor<double>(P, xperp, dt, c->g.V, nrhs, s);
+        launch_unpack_spinor<double>(Y, ys, dt, c->g.V, nrhs, s);
+    } else {
+        launch_unpack_spinor<float>(P, xperp, dt, c->g.V, nrhs, s);
+        launch_unpack_spinor<float>(Y, ys, dt, c->g.V, nrhs, s);
+    }
+    CKL();
+    return OV_OK;
 }
 
 int deflate(ov_ctx* c, double phase, const void* V, const double* lambda, int n_ev, int dtype, ov_stream_t stream) {
@@ -1247,7 +1374,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     }
     if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
     CK(cudaStreamSynchronize(s));
-    if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "eigensolver: a bounded device wait ran out");
+    if (take_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "eigensolver: a bounded device wait ran out");
     {
         char buf[256];
         snprintf(buf, sizeof(buf),
@@ -2213,7 +2340,7 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
     launch_unpack_spinor<double>(X, x, OV_C128, V, nrhs, s);
     CKL();
     CK(cudaStreamSynchronize(s));
-    if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "solve_overlap: a bounded device wait ran out");
+    if (take_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "solve_overlap: a bounded device wait ran out");
     c->info = hist;
     if (st) {
         st->status = status;
@@ -2434,7 +2561,7 @@ extern "C" int ov_eigensolve_overlap(ov_ctx* c, double phase, int chirality, int
     TRY(lanczos_overlap(c, phase, chirality, n_ev, K, tol > 0.0 ? tol : 1e-4, max_restarts >= 0 ? max_restarts : 50, s));
     TRY(dspace_fp64(c, *find_dspace(c, phase, chirality), s));
     CK(cudaStreamSynchronize(s));
-    if (take_wait_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "D_ov Lanczos: a bounded device wait ran out");
+    if (take_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "D_ov Lanczos: a bounded device wait ran out");
     const DefSpace* sp = find_dspace(c, phase, chirality);
     for (int i = 0; i < n_ev; ++i) {
         if (theta_out) theta_out[i] = sp->theta[i];

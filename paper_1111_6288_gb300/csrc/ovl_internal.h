@@ -152,6 +152,20 @@ template <typename R>
 void small_space_project(const void* V, int na, const double* d_signs, const void* X, int nb, void* Xp, void* Ys,
                          long long n, double2* d_C, double2* d_partial, long long partial_cap, cudaStream_t s);
 
+// ---- tensor-core projection: proj_tc.cu --------------------------------------------------
+// The same projection as small_space_project for FP32 vectors on the tcgen05 tensor cores (TF32 with
+// the three-term split, FP32-accurate): C = V^+ X by a split-K GEMM (partials in d_partial, at least
+// 152 x na x min(nb, 32) double2), then X - V C and V diag(s) C; groups of up to 32 right-hand sides.
+// d_img: tc_project_image_bytes(na) bytes of scratch for the pre-split coefficients.  na <= kTcMaxBank.
+constexpr int kTcMaxBank = 384;
+size_t tc_project_image_bytes(int na);
+bool tc_project_available();
+cudaError_t small_space_project_tc(const void* V, int na, const double* d_signs, const void* X, int nb, void* Xp,
+                                   void* Ys, long long n, double2* d_C, double2* d_partial, long long partial_cap,
+                                   void* d_img, cudaStream_t s);
+// 1 if a bounded wait of a tensor-core kernel ran out since the last call (and clears it), else 0; -1 on error.
+int take_tc_timeouts();
+
 // Partial-sum buffer size (double2 elements) needed by dot_rhs/norm2_rhs.
 constexpr int kRedBlocks = 608;
 
