@@ -287,10 +287,11 @@ def kernel_case(dims, precision="f32", shape=0):
     import paper_1111_6288_gb300 as P
     import synth
 
-    prec = P.OV_PREC_F32 if precision == "f32" else P.OV_PREC_F64
+    prec = {"f32": P.OV_PREC_F32, "f64": P.OV_PREC_F64, "f16": P.OV_PREC_F16, "bf16": P.OV_PREC_BF16}[precision]
     U = torch.from_numpy(synth.random_su3_field(dims, LINK_EPS, 0)).cuda()
     ctx = P.Context(P.Params(dims=dims, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=4, precision=prec,
-                             inner_precision=prec, max_nrhs=1, launch_shape=shape))
+                             inner_precision=P.OV_PREC_F64 if prec == P.OV_PREC_F64 else P.OV_PREC_F32,
+                             max_nrhs=1, launch_shape=shape))
     ctx.set_gauge(U)
     del U
     x = torch.from_numpy(synth.gaussian_spinor(dims, 1, 1)).to(ctx.spinor_dtype()).cuda()
@@ -386,7 +387,8 @@ def main():
                     help="profiling case: a few FP32 Wilson-kernel launches (default 24^3x48), "
                          "then exit without a JSON line")
     ap.add_argument("--kernel-dims", default="24,24,24,48", help="lattice of the profiling case: Lx,Ly,Lz,Lt")
-    ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"], help="precision of the profiling case")
+    ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64", "f16", "bf16"],
+                    help="precision of the profiling case")
     ap.add_argument("--kernel-shape", type=int, default=0,
                     help="launch shape of the profiling case (ov_params.launch_shape; 0 = timed by the library)")
     ap.add_argument("--multimass-case", action="store_true",
