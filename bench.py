@@ -371,6 +371,91 @@ def multimass_case(n_defl):
     ctx.close()
 
 
+BATCH_DIMS = (24, 24, 24, 48)
+BATCH_BC = (2, 0, 0, 2)  # Dirichlet x and t (the field direction and time, Sec. 4)
+BATCH_CHARGES = (2.0 / 3.0, -1.0 / 3.0)
+
+
+def batched_case(args):
+    """The batched configuration: 24^3x48, Dirichlet x and t, 12 spin-colour point sources at each
+    of the field values E in --batch-fields (phases q E for q = 2/3, then -1/3, in that order), the
+    --batch-nev lowest |lambda| eigenvectors of Q per phase (eigensolver to 1e-6, an FP32-level
+    bank; each phase after the first warm-started from the nearest bank), minimax polynomial
+    n = 527 on [4e-4, 1], m = 0.02, every right-hand side solved to 1e-10 in one solve_overlap call,
+    in each inner precision of --batch-inner.  Against it: single-source solves of one source per
+    phase.  Prints one JSON object (a case study, not the bench line)."""
+    import numpy as np
+    import torch
+
+    import paper_1111_6288_gb300 as P
+    import synth
+
+    torch.cuda.set_device(0)
+    fields = [float(v) for v in args.batch_fields.split(",")]
+    phases = []
+    for E in fields:
+        for q in BATCH_CHARGES:
+            ph = q * E
+            if ph not in phases:
+                phases.append(ph)
+    phases = phases[:args.batch_phases]
+    U = torch.from_numpy(synth.random_su3_field(BATCH_DIMS, LINK_EPS, 0)).cuda()
+    out = {"workload": f"24^3x48 Dirichlet x,t, 12 point sources x {len(phases)} field phases, N_ev {args.batch_nev}, "
+                       f"n {DEGREE} minimax, m {MASS}, tol {TOL}", "phases": phases, "runs": {}}
+    b1 = synth.point_sources(BATCH_DIMS)
+    for inner in args.batch_inner.split(","):
+        prec = {"f32": P.OV_PREC_F32, "f16": P.OV_PREC_F16, "bf16": P.OV_PREC_BF16}[inner]
+        nrhs = 12 * len(phases)
+        ctx = P.Context(P.Params(dims=BATCH_DIMS, bc=BATCH_BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE,
+                                 poly_kind=1, precision=prec, inner_precision=prec, max_nrhs=nrhs, adaptive_order=1))
+        ctx.set_gauge(U)
+        t0 = time.perf_counter()
+        eig = []
+        for ph in phases:
+            t1 = time.perf_counter()
+            lam, _ = P.eigensolve_Q(ctx, args.batch_nev, phase=ph, tol=1e-6, max_iter=300, register=True)
+            eig.append({"phase": ph, "seconds": time.perf_counter() - t1, "lambda_min": float(abs(lam).min()),
+                        "lambda_max": float(abs(lam).max()), "info": ctx.last_info})
+            print(f"batched_case {inner}: eigensolver phase {ph:.3e}: {eig[-1]['seconds']:.1f} s", flush=True)
+        setup_s = time.perf_counter() - t0
+        b = torch.from_numpy(np.concatenate([b1] * len(phases))).cuda()
+        ph_rhs = [ph for ph in phases for _ in range(12)]
+        # single-source reference solves (one per phase; the first also times the launch shapes)
+        single = []
+        for ph in phases:
+            bs = b[:1].clone()
+            xs = torch.zeros_like(bs)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st = P.solve_overlap(ctx, bs, xs, MASS, tol=TOL, phase=[ph])
+            torch.cuda.synchronize()
+            single.append({"phase": ph, "seconds": time.perf_counter() - t1, "outer": st.outer_iters,
+                           "inner": st.inner_iters, "wilson": st.dslash_calls, "residual": st.true_residual})
+            print(f"batched_case {inner}: single source phase {ph:.3e}: {single[-1]['seconds']:.1f} s", flush=True)
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = P.solve_overlap(ctx, b, x, MASS, tol=TOL, phase=ph_rhs)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        applies = st.dslash_calls / (2 * DEGREE + 1)
+        single_per_source = sum(r["seconds"] for r in single) / len(single)
+        out["runs"][inner] = {
+            "setup_s": setup_s, "eigensolver": eig, "batch_seconds": secs, "nrhs": nrhs,
+            "seconds_per_source": secs / nrhs, "single_source_seconds": single_per_source,
+            "batch_speedup_per_source": single_per_source / (secs / nrhs),
+            "dov_applies_per_s": applies / secs, "dov_applies_per_s_per_rhs": applies / secs / nrhs,
+            "outer": st.outer_iters, "inner": st.inner_iters, "sign_applies": st.sign_applies,
+            "worst_true_residual": st.true_residual, "cycles": ctx.last_info, "tuning": ctx.tune_info,
+            "single": single}
+        print(f"batched_case {inner}: {nrhs} rhs in {secs:.1f} s ({secs / nrhs:.2f} s per source, single "
+              f"{single_per_source:.2f} s), residual {st.true_residual:.2e}", flush=True)
+        ctx.close()
+    print(json.dumps({"batched_case": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,6 +476,13 @@ def main():
                     help="precision of the profiling case")
     ap.add_argument("--kernel-shape", type=int, default=0,
                     help="launch shape of the profiling case (ov_params.launch_shape; 0 = timed by the library)")
+    ap.add_argument("--batched-case", action="store_true",
+                    help="case study: the batched 24^3x48 configuration (point sources x field phases in one "
+                         "solve), then exit without a bench line")
+    ap.add_argument("--batch-fields", default="0,1e-4", help="field values E of the batched case")
+    ap.add_argument("--batch-phases", type=int, default=2, help="distinct phases q E used (first ones)")
+    ap.add_argument("--batch-nev", type=int, default=100, help="eigenvectors of Q per phase")
+    ap.add_argument("--batch-inner", default="f32", help="inner precisions of the batched case (f32,f16,bf16)")
     ap.add_argument("--multimass-case", action="store_true",
                     help="case study: seven masses by the multi-mass solve against single-mass solves, "
                          "then exit without a bench line")
@@ -403,6 +495,9 @@ def main():
         return
     if args.multimass_case:
         multimass_case(args.n_defl)
+        return
+    if args.batched_case:
+        batched_case(args)
         return
     if args.kernel_case:
         kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision, args.kernel_shape)

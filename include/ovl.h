@@ -269,7 +269,9 @@ int deflate(ov_ctx* ctx, double phase, const void* V, const double* lambda, int 
 /* Compute the n_ev eigenpairs of Q (FP64) of smallest |lambda| at field phase `phase` by
  * Chebyshev-filtered subspace iteration with Rayleigh-Ritz, to residual
  * ||Q v - lambda v|| <= tol.  V_out: device [n_ev][site][4][3] complex128 (may be NULL
- * to only register); lambda_out: host [n_ev] (ascending |lambda|).  If register_bank is
+ * to only register); lambda_out: host [n_ev] (ascending |lambda|).  When a bank is registered for
+ * another phase, the iteration starts from that bank's vectors (the nearest phase's; random vectors
+ * fill the rest of the block).  If register_bank is
  * non-zero the result is also registered as by deflate().  Returns OV_ERR_NOT_CONVERGED
  * (with the best vectors written) after max_iter filter cycles. */
 int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_iter,

@@ -211,6 +211,20 @@ int workspace(ov_ctx* c, const std::string& name, int prec, long long nvec, void
     return OV_OK;
 }
 
+// Free the named workspaces whose names start with prefix (after the stream's work is done).
+int release_workspaces(ov_ctx* c, const std::string& prefix, cudaStream_t s) {
+    CK(cudaStreamSynchronize(s));
+    for (auto it = c->ws.begin(); it != c->ws.end();) {
+        if (it->first.compare(0, prefix.size(), prefix) == 0) {
+            if (it->second.ptr) CK(cudaFree(it->second.ptr));
+            it = c->ws.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return OV_OK;
+}
+
 int ensure_small(ov_ctx* c, long long nmat, long long npartial, int nsys) {
     if (nmat > c->cap_c) {
         if (c->d_C) {
@@ -1297,6 +1311,15 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)W, n12 * m, 0x5eed0f0e1ULL);
     count_launch();
     CKL();
+    // warm start: the bank of the nearest other field phase, if one is registered, replaces the first
+    // random vectors (the field moves the low modes of Q little at the phases of the background-field
+    // method, so the filter then only has to correct them)
+    const Bank* warm = nullptr;
+    for (const Bank& bk : c->banks)
+        if (bk.n > 0 && bk.phase != phase && (!warm || std::fabs(bk.phase - phase) < std::fabs(warm->phase - phase)))
+            warm = &bk;
+    if (warm)
+        CK(cudaMemcpyAsync(W, warm->V64, vec_bytes(c, OV_PREC_F64) * std::min(warm->n, m), cudaMemcpyDeviceToDevice, s));
     launch_convert<double, float>(W, Wf, c->g.V, m, s);
     CKL();
     TRY(cholqr2<float>(c, Wf, m, W2f, s));
@@ -1374,13 +1397,17 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     }
     if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
     CK(cudaStreamSynchronize(s));
+    // the block's ten workspaces (2 n_ev vectors each in FP64 and FP32) are the largest the library
+    // holds; they serve only this call
+    TRY(release_workspaces(c, "eig_", s));
     if (take_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "eigensolver: a bounded device wait ran out");
     {
         char buf[256];
         snprintf(buf, sizeof(buf),
-                 "eigensolver: n_ev %d, block %d, %.1f s (filter f32 %.1f, f64 %.1f, orthonormalise %.1f, "
+                 "eigensolver: n_ev %d, block %d%s, %.1f s (filter f32 %.1f, f64 %.1f, orthonormalise %.1f, "
                  "Rayleigh-Ritz %.1f); per cycle [precision/degree:]worst residual: ",
-                 n_ev, m, since(t_start), t_filter[0], t_filter[1], t_ortho, t_rr);
+                 n_ev, m, warm ? " (warm start from another phase's bank)" : "", since(t_start), t_filter[0],
+                 t_filter[1], t_ortho, t_rr);
         c->info = std::string(buf) + hist;
     }
     if (status != OV_OK)

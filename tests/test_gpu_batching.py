@@ -125,3 +125,54 @@ def test_twelve_sources_two_fields_with_library_banks(P):
         assert float(rel) <= 2e-10
     ctx.close()
     ctx64.close()
+
+
+@pytest.fixture(scope="module")
+def config3_small():
+    """The batched configuration's shape on 4 x 4 x 2 x 4: Dirichlet x and t, two field values, the 12
+    lowest |lambda| eigenvectors of Q per field value from the oracle's dense spectrum, and an interval
+    [eps, 1] that holds the rest of both spectra.  (With m0 = -1.5 the Dirichlet faces carry near-zero
+    surface modes of H_w, |lambda|/||H_w|| from 4e-3 up, so the small space must take a dozen of them.)"""
+    dims, bc = (4, 4, 2, 4), (2, 0, 0, 2)
+    obc = (0.0, 1.0, 1.0, 0.0)
+    U = synth.random_su3_field(dims, 0.3, 0)
+    hw, n_ev = 6.5, 12
+    banks, cut = {}, []
+    for phase in (0.0, 0.3):
+        H = dense.hw_matrix(U, M0, obc, phase)
+        lam, W, lam_all, _ = dense.low_modes(H, hw, n_ev)
+        banks[phase] = (lam, dense.vectors_to_fields(W, synth.site_shape(dims)))
+        cut.append(np.sort(np.abs(lam_all / hw))[n_ev])
+    eps = (0.9 * min(cut)) ** 2
+    return dict(dims=dims, bc=bc, obc=obc, U=U, hw=hw, banks=banks, eps=eps)
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+def test_config3_shape_batched_solve_against_oracle(P, config3_small, inner):
+    """12 spin-colour point sources x 2 field values in one solve_overlap call (24 right-hand sides;
+    48 chiral systems in the inner CG, 24 per bank, so the small-space projection may take the
+    tensor cores), adaptive order, FP32 or FP16-stored inner CG; every column's residual is taken
+    with the oracle's D(m) and must meet the tolerance."""
+    import torch
+
+    d, mass, tol, degree = config3_small, 0.02, 1e-10, 300
+    prec = {"f32": P.OV_PREC_F32, "f16": P.OV_PREC_F16}[inner]
+    ctx = P.Context(P.Params(dims=d["dims"], bc=d["bc"], m0=M0, eps=d["eps"], poly_degree=degree, precision=prec,
+                             inner_precision=prec, max_nrhs=24, adaptive_order=1))
+    ctx.set_gauge(dev(d["U"]))
+    phases = []
+    for phase, (lam, V) in d["banks"].items():
+        P.deflate(ctx, dev(V), lam, phase=phase)
+        phases += [phase] * 12
+    b = np.concatenate([synth.point_sources(d["dims"])] * 2)
+    x = torch.zeros_like(dev(b))
+    st = P.solve_overlap(ctx, dev(b), x, mass, tol=tol, phase=phases)
+    print(f"{inner}: {st.outer_iters} outer, {st.inner_iters} inner; {ctx.last_info}; {ctx.tune_info}")
+    assert st.status == 0 and st.true_residual <= tol
+    xs = x.cpu().numpy()
+    for j in range(24):
+        lam, V = d["banks"][phases[j]]
+        p = ov.OverlapParams(m0=M0, hw_norm=d["hw"], eps=d["eps"], degree=degree, bc=d["obc"])
+        r = b[j] - ov.overlap(d["U"], xs[j], mass, p, ov.SmallSpace.from_eigenpairs(V, lam), phases[j])
+        assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol, j
+    ctx.close()
