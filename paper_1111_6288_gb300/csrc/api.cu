@@ -1297,12 +1297,17 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     const long long n12 = 12LL * c->g.V;
     // the block lives in FP32 while the residuals are well above FP32 resolution (filter,
     // Cholesky-QR and Rayleigh-Ritz all on FP32 vectors), then in FP64
-    void *W, *W2, *QW, *QW2, *tt, *Wf, *W2f, *QWf, *QW2f, *ttf;
+    // Memory: the FP32 block (five sets of m vectors, plus three in the filter) lives until the switch
+    // to FP64, the FP64 block from then on; both are released when the call returns.
+    void *W, *W2 = nullptr, *QW = nullptr, *QW2 = nullptr, *tt = nullptr, *Wf, *W2f, *QWf, *QW2f, *ttf;
     TRY(workspace(c, "eig_W", OV_PREC_F64, m, &W));
-    TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
-    TRY(workspace(c, "eig_QW", OV_PREC_F64, m, &QW));
-    TRY(workspace(c, "eig_QW2", OV_PREC_F64, m, &QW2));
-    TRY(workspace(c, "eig_t", OV_PREC_F64, m, &tt));
+    auto f64_block = [&]() -> int {
+        TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
+        TRY(workspace(c, "eig_QW", OV_PREC_F64, m, &QW));
+        TRY(workspace(c, "eig_QW2", OV_PREC_F64, m, &QW2));
+        TRY(workspace(c, "eig_t", OV_PREC_F64, m, &tt));
+        return OV_OK;
+    };
     TRY(workspace(c, "eig_W", OV_PREC_F32, m, &Wf));
     TRY(workspace(c, "eig_W2", OV_PREC_F32, m, &W2f));
     TRY(workspace(c, "eig_QW", OV_PREC_F32, m, &QWf));
@@ -1331,7 +1336,8 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     // The filter degree is chosen each cycle so that the largest amplification, |T_d(z(0))|
     // with z(0) = -(1 + a)/(1 - a), stays below amp: a larger spread between the filtered
     // columns would collapse the block below the resolution of the Cholesky-QR step.
-    const double switch_res = 3e-6;
+    // FP32 resolves residuals down to a few 1e-7: a target of 2e-6 or more is met without the FP64 phase
+    const double switch_res = tol >= 2e-6 ? 0.0 : 3e-6;
     double prev_worst = 1e300;
     bool in_f64 = false;
     double a = -1.0;  // lower end of the damped interval of Q^2 (set by each Rayleigh-Ritz)
@@ -1347,10 +1353,14 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     for (int it = 0; it <= max_iter; ++it) {
         int degree = 0;
         if (it > 0) {
-            if (!in_f64 && (worst <= switch_res || (worst < 1e-4 && worst > 0.9 * prev_worst))) {
+            if (!in_f64 && (worst <= switch_res || (switch_res > 0.0 && worst < 1e-4 && worst > 0.9 * prev_worst))) {
                 // FP32 -> FP64: widen the block and restore FP64 orthonormality
                 launch_convert<float, double>(Wf, W, c->g.V, m, s);
                 CKL();
+                TRY(release_workspaces(c, "flt_", s));
+                TRY(release_workspaces(c, "eig_W/32", s));
+                for (const char* nm : {"eig_W2/32", "eig_QW/32", "eig_QW2/32", "eig_t/32"}) TRY(release_workspaces(c, nm, s));
+                TRY(f64_block());
                 auto t0 = std::chrono::steady_clock::now();
                 TRY(cholqr2<double>(c, W, m, W2, s));
                 t_ortho += since(t0);
@@ -1388,6 +1398,9 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     if (!in_f64) {  // converged (or stopped) in FP32: hand out FP64 vectors
         launch_convert<float, double>(Wf, W, c->g.V, m, s);
         CKL();
+        TRY(release_workspaces(c, "flt_", s));
+        for (const char* nm : {"eig_W2/32", "eig_QW/32", "eig_QW2/32", "eig_t/32"}) TRY(release_workspaces(c, nm, s));
+        TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
         TRY(cholqr2<double>(c, W, m, W2, s));
     }
     for (int i = 0; i < n_ev; ++i) lambda_out[i] = theta[i];
@@ -1400,6 +1413,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     // the block's ten workspaces (2 n_ev vectors each in FP64 and FP32) are the largest the library
     // holds; they serve only this call
     TRY(release_workspaces(c, "eig_", s));
+    TRY(release_workspaces(c, "flt_", s));
     if (take_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "eigensolver: a bounded device wait ran out");
     {
         char buf[256];
