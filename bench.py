@@ -456,6 +456,83 @@ def batched_case(args):
     print(json.dumps({"batched_case": out}), flush=True)
 
 
+def derivative_case(args):
+    """The field derivative at the configuration of the background-field runs: 16^3x32, Dirichlet x and
+    t, links exp(i 0.2 H), 50 eigenvectors of Q per phase (recomputed at every phase), minimax n = 527 on
+    [4e-4, 1], m = 0.02, the 12 spin-colour point sources at (8, 0, 0, 8), charge 2/3, E = 1e-4.
+    dC(t)/dE by the tangent solve (ov_dcorr_dE) against central differences of C at E +- h for
+    h = 1e-5 and 5e-6 (solves to 1e-13, the eigen-split recomputed at each E), with the Richardson
+    estimate and the difference of the two steps as the finite difference's noise floor; then the
+    derivative from solves to 1e-6 with FP32 and with BF16-stored inner CGs, with their error against
+    the 1e-13 one.  Prints one JSON object (a case study, not the bench line)."""
+    import numpy as np
+    import torch
+
+    import paper_1111_6288_gb300 as P
+    import synth
+
+    torch.cuda.set_device(0)
+    dims, bc, charge, E, h = DIMS, (2, 0, 0, 2), 2.0 / 3.0, 1e-4, 1e-5
+    U = torch.from_numpy(synth.random_su3_field(dims, LINK_EPS, 0)).cuda()
+    src = torch.from_numpy(synth.point_sources(dims, site=(8, 0, 0, 8))).cuda()
+    Es = [E, E + h, E - h, E + h / 2, E - h / 2]
+    out = {"workload": f"16^3x32 Dirichlet x,t, 12 point sources, N_ev {args.deriv_nev}, n {DEGREE}, m {MASS}, "
+                       f"q {charge:.4f}, E {E}", "steps": [h, h / 2]}
+    t0 = time.perf_counter()
+
+    def context(prec, inner):
+        ctx = P.Context(P.Params(dims=dims, bc=bc, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE, poly_kind=1,
+                                 precision=prec, inner_precision=inner, max_nrhs=12, adaptive_order=1))
+        ctx.set_gauge(U)
+        return ctx
+
+    ctx = context(P.OV_PREC_F64, P.OV_PREC_F32)
+    banks = {}
+    for e in Es:
+        lam, V = P.eigensolve_Q(ctx, args.deriv_nev, phase=charge * e, tol=1e-11, max_iter=300, register=True,
+                                want_vectors=True)
+        banks[e] = (lam, V)
+    out["setup_s"] = time.perf_counter() - t0
+    print(f"derivative_case: banks for {len(Es)} phases in {out['setup_s']:.1f} s", flush=True)
+    t1 = time.perf_counter()
+    C0, dC = P.correlator_jacobian(ctx, src, E, charge, MASS, tol=1e-13)
+    out["tangent_s"] = time.perf_counter() - t1
+    Cs = {}
+    for e in Es[1:]:
+        x = torch.zeros_like(src)
+        P.solve_overlap(ctx, src, x, MASS, tol=1e-13, phase=[charge * e] * 12)
+        Cs[e] = P.correlator(ctx, x)
+    fd1 = (Cs[E + h] - Cs[E - h]) / (2 * h)
+    fd2 = (Cs[E + h / 2] - Cs[E - h / 2]) / h
+    rich = (4 * fd2 - fd1) / 3
+    scale = float(np.abs(fd1).max())
+    out.update({"C": C0.tolist(), "dC_dE": dC.tolist(), "fd_h": fd1.tolist(), "fd_h2": fd2.tolist(),
+                "rel_err_vs_fd_h": float(np.abs(dC - fd1).max()) / scale,
+                "rel_err_vs_fd_h2": float(np.abs(dC - fd2).max()) / scale,
+                "rel_err_vs_richardson": float(np.abs(dC - rich).max()) / scale,
+                "fd_noise_floor": float(np.abs(fd1 - fd2).max()) / scale,
+                "max_abs_dC": float(np.abs(dC).max()), "max_abs_C": float(np.abs(C0).max())})
+    print(f"derivative_case: dC/dE vs FD: {out['rel_err_vs_fd_h']:.2e} (h), {out['rel_err_vs_fd_h2']:.2e} (h/2), "
+          f"{out['rel_err_vs_richardson']:.2e} (Richardson); FD noise floor {out['fd_noise_floor']:.2e}", flush=True)
+    ctx.close()
+    # lower-precision variants: solves to 1e-6 with FP32 / BF16-stored inner CGs, same banks
+    variants = {}
+    for name, prec in (("f32", P.OV_PREC_F32), ("bf16", P.OV_PREC_BF16)):
+        cv = context(prec, prec)
+        lam, V = banks[E]
+        P.deflate(cv, V, lam, phase=charge * E)
+        t1 = time.perf_counter()
+        Cv, dCv = P.correlator_jacobian(cv, src, E, charge, MASS, tol=1e-6)
+        variants[name] = {"seconds": time.perf_counter() - t1,
+                          "rel_err_dC_vs_f64": float(np.abs(dCv - dC).max()) / float(np.abs(dC).max()),
+                          "rel_err_C_vs_f64": float(np.abs(Cv - C0).max()) / float(np.abs(C0).max()),
+                          "rel_err_dC_vs_fd_h": float(np.abs(dCv - fd1).max()) / scale}
+        print(f"derivative_case {name}: {variants[name]}", flush=True)
+        cv.close()
+    out["variants"] = variants
+    print(json.dumps({"derivative_case": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,6 +560,10 @@ def main():
     ap.add_argument("--batch-phases", type=int, default=2, help="distinct phases q E used (first ones)")
     ap.add_argument("--batch-nev", type=int, default=100, help="eigenvectors of Q per phase")
     ap.add_argument("--batch-inner", default="f32", help="inner precisions of the batched case (f32,f16,bf16)")
+    ap.add_argument("--derivative-case", action="store_true",
+                    help="case study: dC/dE at 16^3x32 against central finite differences in E, then exit "
+                         "without a bench line")
+    ap.add_argument("--deriv-nev", type=int, default=50, help="eigenvectors of Q per phase in the derivative case")
     ap.add_argument("--multimass-case", action="store_true",
                     help="case study: seven masses by the multi-mass solve against single-mass solves, "
                          "then exit without a bench line")
@@ -498,6 +579,9 @@ def main():
         return
     if args.batched_case:
         batched_case(args)
+        return
+    if args.derivative_case:
+        derivative_case(args)
         return
     if args.kernel_case:
         kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision, args.kernel_shape)
@@ -586,6 +670,7 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     launches = P.launch_count() - launches0
+    mixed_cycles = ctx_mix.last_info  # before later calls on this context replace it
     barrier(world)
     clk = clocks.stop()
     ctx_mix.set_profiling(False)
@@ -737,7 +822,7 @@ def main():
                                  "mixed_outer_iters": stats[0].outer_iters, "mixed_inner_iters": stats[0].inner_iters,
                                  "mixed_sign_applies": stats[0].sign_applies,
                                  "mixed_wilson_applies": stats[0].dslash_calls,
-                                 "mixed_cycles": ctx_mix.last_info,
+                                 "mixed_cycles": mixed_cycles,
                                  "mixed_true_residual": worst_res, "fp64": fp64},
             "dov_apply_per_s": {"f32": rate32, "f64": rate64, **rates_half},
             "dov_error_vs_f64": errors,

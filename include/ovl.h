@@ -127,7 +127,10 @@ typedef struct ov_solve_stats {
     int inner_iters;        /* inner CG iterations, summed over cycles */
     long long sign_applies; /* sign(H_w) applications, summed over right-hand sides */
     long long dslash_calls; /* Wilson-operator applications, summed over right-hand sides */
-    double true_residual;   /* max over rhs of ||b - D(m) x|| / ||b||, FP64 operator */
+    double true_residual;   /* max over rhs of ||b - D(m) x|| / ||b||, FP64 operator (in FP32 and
+                               16-bit inner precisions, once every residual is <= min(1e-6, 1e4 tol)
+                               the FP64 residual is updated as r - D(m) e with D(m) e applied in FP32,
+                               whose rounding, ~1e-6 |r|, is below tol / 100) */
     double seconds;         /* wall time of the solve */
 } ov_solve_stats;
 
@@ -298,7 +301,7 @@ int ov_set_projection(ov_ctx* ctx, int method);
  * the FP64 operator apply_overlap computes.  b, x: device [nrhs][site][4][3] complex128;
  * x is the initial guess on input and the solution on output; b != x.
  * phase: host [nrhs] (NULL = all zero).  Outer loop: FP64 true residual and FP64 update
- * of x.  Inner loop: CG in ctx inner_precision on the chiral-sector normal operator
+ * of x (with an FP32 image of small corrections in the FP64 residual, see ov_solve_stats).  Inner loop: CG in ctx inner_precision on the chiral-sector normal operator
  * P_s [2(1 - m^2/4)(1 + s sign(H_w)) + m^2] P_s (one sign application per iteration and
  * sector), then the correction D(m)^+ y.  stats: host, may be NULL. */
 int solve_overlap(ov_ctx* ctx, double mass, const double* phase, const void* b, void* x,

@@ -165,3 +165,34 @@ def test_dC_dE_matches_oracle_finite_difference(P):
     want = float(np.dot(g, fd))
     assert abs(Et.grad.item() - want) < 1e-5 * abs(want)
     ctx.close()
+
+
+def test_dC_dE_config4_shape_against_library_finite_difference(P):
+    """The background-field configuration's derivative at a size the test suite affords: 8 x 4 x 4 x 8,
+    Dirichlet x and t, 16 eigenvectors of Q per phase from the library's eigensolver (recomputed at
+    E +- h), the minimax polynomial n = 527 on [4e-4, 1], m = 0.02, the 12 point sources, q = 2/3,
+    E = 1e-4: dC/dE from the tangent solve (ov_dcorr_dE) against the central difference of C at
+    E +- 1e-5 from FP64-accurate solves (1e-13), to 1e-5 of the largest |dC/dE|.  (The library's FP64
+    operator and solve are pinned against the oracle at small size by the other tests; the full-size
+    case runs as bench.py --derivative-case.)"""
+    import torch
+
+    dims, bc, mass, charge, E, h = (8, 4, 4, 8), (2, 0, 0, 2), 0.02, 2.0 / 3.0, 1e-4, 1e-5
+    U = dev(synth.random_su3_field(dims, 0.2, 0))
+    ctx = P.Context(P.Params(dims=dims, bc=bc, m0=M0, eps=4e-4, poly_degree=527, poly_kind=1, precision=0,
+                             inner_precision=1, max_nrhs=12, adaptive_order=1))
+    ctx.set_gauge(U)
+    for e in (E, E + h, E - h):
+        P.eigensolve_Q(ctx, 16, phase=charge * e, tol=1e-11, max_iter=300)
+    src = dev(synth.point_sources(dims, site=(4, 0, 0, 4)))
+    C0, dC = P.correlator_jacobian(ctx, src, E, charge, mass, tol=1e-13)
+    Cs = {}
+    for e in (E + h, E - h):
+        x = torch.zeros_like(src)
+        P.solve_overlap(ctx, src, x, mass, tol=1e-13, phase=[charge * e] * 12)
+        Cs[e] = P.correlator(ctx, x)
+    fd = (Cs[E + h] - Cs[E - h]) / (2 * h)
+    err = float(np.abs(dC - fd).max() / np.abs(fd).max())
+    print(f"config-4 shape: dC/dE vs FD {err:.2e}, max |dC/dE| {np.abs(dC).max():.3e}")
+    assert err < 1e-5
+    ctx.close()
