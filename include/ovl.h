@@ -105,9 +105,9 @@ typedef struct ov_params {
     double inner_tol;     /* relative tolerance of each inner solve (<= 0: default,
                              1e-6 for F32; for F64 the outer target itself) */
     int launch_shape;     /* Wilson-kernel launch shape of the polynomial loops: 0 = timed per
-                             batch size (ov_tune_info); else 1, 2 or 4 systems per thread block,
-                             | 8 for the FP32 register budget of 7 blocks per SM instead of 6,
-                             | 16 for the kernel that stages x-rows in shared memory (used where
+                             batch size (ov_tune_info); else 1, 2, 4 or 8 systems per thread block,
+                             | 16 for the FP32 register budget of 7 blocks per SM instead of 6,
+                             | 32 for the kernel that stages x-rows in shared memory (used where
                              the lattice allows it, see ov_tune_info). */
     int poly_kind;        /* coeffs = NULL: 0 = Chebyshev interpolant of x^{-1/2} (ov_chebyshev_coeffs),
                              1 = the polynomial of least relative error max |1 - sqrt(x) P(x)|
@@ -157,7 +157,7 @@ const char* ov_last_error(const ov_ctx* ctx);
 /* Human-readable summary of the last eigensolver or solve call on ctx (cycles, residuals). */
 const char* ov_last_info(const ov_ctx* ctx);
 /* Timings of the Wilson-kernel launch shapes the library tried for each batch size it met
- * (1, 2 or 4 systems per thread block; "d": FP32 registers capped for 7 resident blocks per SM
+ * (1, 2, 4 or 8 systems per thread block; "d": FP32 registers capped for 7 resident blocks per SM
  * instead of 6; "t": the kernel that stages whole x-rows in shared memory with bulk copies,
  * offered when Lx is a multiple of 4 and rows of Lx sites tile a 32-multiple block); the
  * fastest is used from then on. */

@@ -387,7 +387,7 @@ int tuned_shape(ov_ctx* c, int ns, const void* U, const double* d_phase, void* i
     auto it = c->launch_shape.find(key);
     if (it != c->launch_shape.end()) return it->second;
     std::vector<int> shapes;
-    for (int by : {1, 2, 4}) {
+    for (int by : {1, 2, 4, 8}) {
         if (by > ns) break;
         shapes.push_back(by);
         if (!std::is_same<R, double>::value) {
@@ -1025,7 +1025,7 @@ int ov_create(const ov_params* p, ov_ctx** out) {
     {
         const int rb = p->launch_shape & kShapeRhsMask;
         if (p->launch_shape < 0 || (p->launch_shape & ~(kShapeRhsMask | kShapeDense | kShapeTiled)) ||
-            (p->launch_shape > 0 && rb != 1 && rb != 2 && rb != 4))
+            (p->launch_shape > 0 && rb != 1 && rb != 2 && rb != 4 && rb != 8))
             return fail(c, OV_ERR_ARG, "launch_shape = %d invalid", p->launch_shape);
     }
     c = new ov_ctx();

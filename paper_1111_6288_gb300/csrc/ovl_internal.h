@@ -66,13 +66,13 @@ struct Epilogue {
 // S: storage type (double, float, H16, B16; the 16-bit ones compute in FP32).
 // deriv: apply dH_w/dphi (the phi-derivative of the x hops, per right-hand-side phase) in
 // place of H_w; the epilogue is the same.  shape: right-hand sides per thread block in the
-// low bits (1, 2 or 4; 0 = default), | kShapeDense for the FP32 kernel whose registers allow
+// low bits (1, 2, 4 or 8; 0 = default), | kShapeDense for the FP32 kernel whose registers allow
 // 7 resident blocks per SM instead of 6 (no effect in FP64).
 // | kShapeTiled: the FP32 / 16-bit kernel that stages whole x-rows in shared memory (lattices
 // for which tile_rows() > 0; otherwise the plain kernel runs).
-constexpr int kShapeRhsMask = 7;
-constexpr int kShapeDense = 8;
-constexpr int kShapeTiled = 16;
+constexpr int kShapeRhsMask = 15;
+constexpr int kShapeDense = 16;
+constexpr int kShapeTiled = 32;
 // Rows of x per block of the tiled kernel for `by` right-hand sides per block (0: not tileable).
 int tile_rows(const Geom& g, int by);
 // 1 if a bounded device wait ran out since the last call (and clears it), 0 if not, -1 on error.

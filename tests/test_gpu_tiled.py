@@ -1,7 +1,7 @@
 """The Wilson kernel that stages whole x-rows in shared memory (bulk copies on an mbarrier).
 
 On lattices whose x-rows tile a thread block (Lx a multiple of 4, rows x Lx a multiple of 32
-sites), launch_shape | 16 selects it.  It must agree with the oracle like the plain kernel and
+sites), launch_shape | 32 selects it.  It must agree with the oracle like the plain kernel and
 give the same bits as the plain kernel, which accumulates the hops in the same order (z, t,
 x, y), for every right-hand-side block and register budget, in FP32 and 16-bit storage.
 """
@@ -20,7 +20,7 @@ BC_NUM = {0: 1.0, 1: -1.0, 2: 0.0}
 DIMS, BC = (8, 8, 4, 6), (2, 0, 1, 2)  # 384-site slices of 8 rows; Dirichlet x, t, antiperiodic z
 PHASES = [0.3, 0.0, -0.2]
 TOL = {1: 2e-6, 2: 16 * 2.0 ** -11, 3: 16 * 2.0 ** -8}  # one H_w (see test_gpu_parity / test_gpu_half)
-TILED = [1 | 16, 1 | 8 | 16, 2 | 16, 4 | 16]
+TILED = [1 | 32, 1 | 16 | 32, 2 | 32, 4 | 32]
 
 
 def obc(bc):
@@ -68,7 +68,7 @@ def test_tiled_wilson_matches_oracle(P, precision, shape):
     want = np.stack([dirac.hermitian_wilson(U, x[j], M0, obc(BC), PHASES[j]) for j in range(3)])
     err = float(np.abs(got - want).max() / np.abs(want).max())
     assert err < TOL[precision], err
-    plain = run(P, ctx_for(P, precision, shape & 7), P.apply_wilson, x, phase=PHASES, hermitian=True)
+    plain = run(P, ctx_for(P, precision, shape & 15), P.apply_wilson, x, phase=PHASES, hermitian=True)
     assert np.array_equal(plain, got.astype(np.complex64))
     ctx.close()
 

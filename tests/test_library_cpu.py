@@ -82,7 +82,7 @@ def test_host_eigh_degenerate(ovl):
 @pytest.mark.parametrize("bad", [dict(dims=(1, 4, 4, 4)), dict(eps=0.0), dict(eps=1.0), dict(poly_degree=0),
                                  dict(precision=7), dict(max_nrhs=0), dict(bc=(0, 0, 0, 5)),
                                  dict(inner_precision=2), dict(inner_precision=3), dict(launch_shape=3),
-                                 dict(launch_shape=32), dict(launch_shape=-1), dict(poly_kind=2)])
+                                 dict(launch_shape=64), dict(launch_shape=-1), dict(poly_kind=2)])
 def test_create_rejects_invalid_parameters(ovl, bad):
     kw = dict(dims=(4, 4, 4, 4))
     kw.update(bad)
@@ -108,7 +108,7 @@ def test_create_accepts_16bit_storage(ovl, precision):
         ovl.Context(ovl.Params(dims=(4, 4, 4, 4), precision=ovl.OV_PREC_F32, inner_precision=precision))
 
 
-@pytest.mark.parametrize("shape", [1, 2 | 16, 4 | 8 | 16])
+@pytest.mark.parametrize("shape", [1, 2 | 32, 4 | 16 | 32, 8, 8 | 16])
 def test_create_accepts_launch_shapes(ovl, shape):
     ovl.Context(ovl.Params(dims=(4, 4, 4, 4), launch_shape=shape)).close()
 
