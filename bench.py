@@ -537,6 +537,55 @@ def batched_case(args):
     print(json.dumps({"batched_case": out}), flush=True)
 
 
+def precision_case(args):
+    """The bench's solve (16^3x32, 50 H_w modes, 32 D_ov low modes per chiral sector, adaptive order,
+    minimax n = 527, m = 0.02, one point source, 1e-10) with each inner precision: FP32, FP16- and
+    BF16-stored polynomial loops (FP32 arithmetic), and FP64 with the same algorithm.  Each 16-bit
+    run uses a context of that storage (its 16-bit links) with the same bank and its own D_ov
+    low modes.  Prints one JSON object (a case study, not the bench line)."""
+    import torch
+
+    import paper_1111_6288_gb300 as P
+    import synth
+
+    torch.cuda.set_device(0)
+    U = torch.from_numpy(synth.random_su3_field(DIMS, LINK_EPS, 0)).cuda()
+    common = dict(dims=DIMS, bc=BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE, max_nrhs=2, poly_kind=1,
+                  adaptive_order=1)
+    c64 = P.Context(P.Params(precision=P.OV_PREC_F64, inner_precision=P.OV_PREC_F64, **common))
+    c64.set_gauge(U)
+    lam, V = P.eigensolve_Q(c64, N_EV, tol=1e-10, max_iter=200, register=False, want_vectors=True)
+    c64.close()
+    b = torch.from_numpy(synth.point_sources(DIMS, [(0, 0)])).cuda()
+    out = {"workload": WORKLOAD, "runs": {}}
+    for name, prec in (("f32", P.OV_PREC_F32), ("f16", P.OV_PREC_F16), ("bf16", P.OV_PREC_BF16)):
+        ctx = P.Context(P.Params(precision=prec, inner_precision=prec, **common))
+        ctx.set_gauge(U)
+        P.deflate(ctx, V, lam)
+        for chi in (1, -1):
+            P.eigensolve_overlap(ctx, args.n_defl, chirality=chi)
+        arms = [(name, prec)] + ([("f64_same_algorithm", P.OV_PREC_F64)] if name == "f32" else [])
+        for arm, inner in arms:
+            ctx.set_inner_precision(inner)
+            x = torch.zeros_like(b)
+            P.solve_overlap(ctx, b, x, MASS, tol=TOL)  # launch shapes, graphs
+            times = []
+            for _ in range(2):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = P.solve_overlap(ctx, b, x, MASS, tol=TOL, raise_on_error=False)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            out["runs"][arm] = {"seconds": min(times), "status": st.status, "outer": st.outer_iters,
+                                "inner": st.inner_iters, "sign_applies": st.sign_applies,
+                                "true_residual": st.true_residual, "cycles": ctx.last_info}
+            print(f"precision_case {arm}: {min(times):.2f} s, {st.outer_iters} outer, {st.inner_iters} inner, "
+                  f"residual {st.true_residual:.2e}", flush=True)
+        ctx.close()
+    print(json.dumps({"precision_case": out}), flush=True)
+
+
 def derivative_case(args):
     """The field derivative at the configuration of the background-field runs: 16^3x32, Dirichlet x and
     t, links exp(i 0.2 H), 50 eigenvectors of Q per phase (recomputed at every phase), minimax n = 527 on
@@ -641,6 +690,9 @@ def main():
     ap.add_argument("--batch-phases", type=int, default=2, help="distinct phases q E used (first ones)")
     ap.add_argument("--batch-nev", type=int, default=100, help="eigenvectors of Q per phase")
     ap.add_argument("--batch-inner", default="f32", help="inner precisions of the batched case (f32,f16,bf16)")
+    ap.add_argument("--precision-case", action="store_true",
+                    help="case study: the bench's solve with FP32, FP16-, BF16-stored and FP64 inner CGs, then "
+                         "exit without a bench line")
     ap.add_argument("--derivative-case", action="store_true",
                     help="case study: dC/dE at 16^3x32 against central finite differences in E, then exit "
                          "without a bench line")
@@ -663,6 +715,9 @@ def main():
         return
     if args.derivative_case:
         derivative_case(args)
+        return
+    if args.precision_case:
+        precision_case(args)
         return
     if args.kernel_case:
         kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision, args.kernel_shape)

@@ -128,9 +128,10 @@ typedef struct ov_solve_stats {
     long long sign_applies; /* sign(H_w) applications, summed over right-hand sides */
     long long dslash_calls; /* Wilson-operator applications, summed over right-hand sides */
     double true_residual;   /* max over rhs of ||b - D(m) x|| / ||b||, FP64 operator (in FP32 and
-                               16-bit inner precisions, once every residual is <= min(1e-6, 1e4 tol)
-                               the FP64 residual is updated as r - D(m) e with D(m) e applied in FP32,
-                               whose rounding, ~1e-6 |r|, is below tol / 100) */
+                               16-bit inner precisions, once every residual is <= min(1e-5, 1e5 tol)
+                               the FP64 residual is updated as r - D(m) e with D(m) e from FP32
+                               applications to the FP32 hi and lo parts of e, whose rounding,
+                               ~1e-6 |r|, is below tol / 10) */
     double seconds;         /* wall time of the solve */
 } ov_solve_stats;
 

@@ -2368,23 +2368,35 @@ int solve_impl(ov_ctx* c, double mass, const SysSet& Srhs, const void* b, void* 
         CKL();
         ++outer;
         // The new residual b - D(m) (x + e) = r - D(m) e.  While r is large, D(m) (x + e) is applied in
-        // FP64.  Once every |r_j| <= theta |b_j| the FP64 sum r - D(m) e takes D(m) e from an FP32
-        // application instead: its rounding, about 1e-6 of |D(m) e| ~ |r| (including e rounded to
-        // FP32), stays below tol / 100 for theta = min(1e-6, 1e4 tol), and one FP32 application costs
-        // a tenth of an FP64 one on this GPU.
+        // FP64.  Once every |r_j| <= theta |b_j| (FP32 and 16-bit inner precisions), the FP64 sum
+        // r - D(m) e takes D(m) e from two FP32 applications, to e_hi = fl32(e) and e_lo = fl32(e - e_hi)
+        // (so e itself enters to 2^-48): their rounding is about 1e-6 of |D(m) e| ~ |r|, below tol / 10
+        // for theta = min(1e-5, 1e5 tol), and two FP32 applications cost a fifth of one FP64 application
+        // on this GPU.
         double worst_prev = 0.0;
         for (int j = 0; j < nrhs; ++j) worst_prev = std::max(worst_prev, res[j]);
-        const double theta = std::min(1e-6, 1e4 * tol);
+        const double theta = std::min(1e-5, 1e5 * tol);
         const bool fp32_update = std::is_same<R, float>::value && worst_prev <= theta;  // FP64 solves stay FP64
         if (fp32_update) {
-            void *e32, *de32;
-            TRY(workspace(c, "sol_e32", OV_PREC_F32, nrhs, &e32));
-            TRY(workspace(c, "sol_de32", OV_PREC_F32, nrhs, &de32));
-            launch_convert<double, float>(E64, e32, V, nrhs, s);
+            void *e32, *de32, *t64;
+            TRY(workspace(c, "sol_e32", OV_PREC_F32, 2 * nrhs, &e32));
+            TRY(workspace(c, "sol_de32", OV_PREC_F32, 2 * nrhs, &de32));
+            TRY(workspace(c, "sol_t64", OV_PREC_F64, nrhs, &t64));
+            const size_t vb32 = vec_bytes(c, OV_PREC_F32);
+            char* e_lo = (char*)e32 + vb32 * nrhs;
+            launch_convert<double, float>(E64, e32, V, nrhs, s);   // e_hi
+            launch_convert<float, double>(e32, t64, V, nrhs, s);
+            launch_axpby<double>(ones.data(), E64, mones.data(), t64, n12, nrhs, s);  // e - e_hi
+            launch_convert<double, float>(t64, e_lo, V, nrhs, s);  // e_lo
             CKL();
-            TRY(overlap_op<float>(c, e32, Srhs, mass, false, de32, s));
+            SysSet S2 = Srhs;
+            S2.n = 2 * nrhs;
+            S2.phase.insert(S2.phase.end(), Srhs.phase.begin(), Srhs.phase.end());
+            TRY(overlap_op<float>(c, e32, S2, mass, false, de32, s));
             launch_convert<float, double>(de32, DX, V, nrhs, s);
-            launch_axpby<double>(mones.data(), DX, ones.data(), Rr, n12, nrhs, s);  // R -= D e
+            launch_axpby<double>(mones.data(), DX, ones.data(), Rr, n12, nrhs, s);  // R -= D e_hi
+            launch_convert<float, double>((char*)de32 + vb32 * nrhs, DX, V, nrhs, s);
+            launch_axpby<double>(mones.data(), DX, ones.data(), Rr, n12, nrhs, s);  // R -= D e_lo
             CKL();
             norm2_rhs<double>(Rr, n12, nrhs, rn2.data(), c->d_partial, c->d_red, s);
             for (int j = 0; j < nrhs; ++j) {

@@ -13,13 +13,14 @@
 // a_lo = tf32(a - a_hi)): a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, relative error ~2^-21 per
 // product, FP32 accumulation in tensor memory (TMEM), FP64 sums of the per-CTA partials.
 //
-// Data path: TMA (cp.async.bulk.tensor, this GPU's memory, no multicast) brings raw FP32 tiles of
-// V and X into shared memory through a 4-stage mbarrier pipeline; all threads split each tile into
-// the hi/lo operand tiles (128-byte swizzled, K-major: one 128-byte row of 32 floats per matrix row)
-// and one thread issues tcgen05.mma (kind::tf32, M = 128, cta_group::1) into a TMEM accumulator,
-// read back with tcgen05.ld for the epilogue.  Every wait on a barrier is bounded (about a second);
-// a wait that runs out records the timeout in g_tc_timeouts, the block waits (bounded) for the
-// copies it issued and frees its TMEM before it returns.
+// Data path, one warp-specialised block per SM: a producer warp brings raw FP32 tiles of V and X into
+// shared memory by TMA (cp.async.bulk.tensor, this GPU's memory, no multicast) through a multi-stage
+// mbarrier pipeline; four warps split each tile into the hi/lo operand tiles (128-byte swizzled,
+// K-major: one 128-byte row of 32 floats per matrix row); one thread issues tcgen05.mma (kind::tf32,
+// M = 128, cta_group::1) into TMEM accumulators, which the four warps read back with tcgen05.ld.
+// Every wait on a barrier is bounded (about a second); a wait that runs out records the timeout in
+// g_tc_timeouts and makes every role of the block stop; the block then waits (bounded) for the copies
+// and MMAs it started and frees its TMEM before it returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -33,7 +34,6 @@
 namespace ovl {
 namespace {
 
-constexpr int TC_THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) ...
 constexpr int KT = 32;            // floats per K-tile row: one 128-byte swizzle span
 constexpr int ROW_BYTES = KT * 4;  // 128
 constexpr long long kTcWaitCycles = 2000000000LL;  // about one second at the SM clock
@@ -138,9 +138,31 @@ __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
     lo = make_float4(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y), tf32_round(v.z - hi.z), tf32_round(v.w - hi.w));
 }
 
-// Columns of the TMEM accumulator: a power of two >= 32 covering n.
+// Columns of the TMEM accumulator: a power of two >= 32 covering n (at most 512, all of TMEM).
 __host__ __device__ constexpr uint32_t tmem_cols(int n) {
-    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : 256u;
+    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
+}
+
+// One arrival on bar (no transaction bytes).
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Wait of one role of a warp-specialised block: phase `parity` of bar, for at most about a second, and
+// no longer once another role has given up (abort set).  false: the wait ran out (recorded in
+// g_tc_timeouts, abort set) or the block is aborting.
+__device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    int spins = 0;
+    while (!bar_try_wait(bar, parity)) {
+        if ((++spins & 31) == 0 && *abort) return false;
+        if (clock64() - t0 > kTcWaitCycles) {
+            atomicExch(&g_tc_timeouts, 1);
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
 }
 
 // 8 consecutive FP32 columns of this thread's TMEM lane.
@@ -156,14 +178,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 
 // ---- C = V^+ X: split over the contraction ------------------------------------------------
 //
-// Grid (nchunk, ceil(na / 128)), 128 threads.  Block (cx, my) takes K-tiles [cx tpc, (cx + 1) tpc) of
-// 32 floats and rows [128 my, 128 my + 128) of V (rows beyond na arrive as zeros from the tensor map),
-// accumulates D = V [X; J X]^T (M = 128, N = 2 KP) in TMEM over its K-tiles and writes its partial
-// C rows, partial[cx][i][j] = (D[i][j], D[i][KP + j]).  Shared memory: S raw stages {V tile 128 rows,
-// X tile KP rows} of 128-byte rows written by TMA with the 128-byte swizzle, and two operand
-// buffers {A_hi, A_lo, B_hi, B_lo} in the same layout: the split keeps every 16-byte chunk at its
-// offset (J X keeps it too, rows KP..2KP-1), so the thread pass is conflict-free and the operand
-// tiles match the swizzle the descriptors name.
+// Grid (nchunk, ceil(na / 128)), 192 threads in three roles that hand tiles over through mbarriers:
+//   warp 0   TMA producer: K-tile i of this block (32 floats of every row) into raw stage i % S,
+//            V rows [128 my, 128 my + 128) (rows beyond na arrive as zeros) and the KP rows of X;
+//   warp 1   MMA issuer (and TMEM owner): D = V [X; J X]^T, M = 128, N = 2 KP, three TF32 products
+//            per K-step, into the accumulator set of the tile's group of G K-tiles;
+//   warps 2-5  split each raw tile into the hi/lo operand tiles (the 128-byte swizzle keeps every
+//            16-byte chunk at its offset, J X too, rows KP..2KP-1), and add each completed group's
+//            accumulators into FP32 registers; at the end they write partial[cx][i][j] = (Re, Im).
+// Barriers: full[s] (TMA bytes), empty[s] (the four transform warps), opfull[b] (transform warps),
+// opempty[b] (MMA commit), accempty[set] (transform warps, once a group's sums are read).
 template <int KP>
 struct VdotLayout {
     static constexpr int S = 4;
@@ -173,160 +197,195 @@ struct VdotLayout {
     static constexpr int OPA = 128 * ROW_BYTES;
     static constexpr int OPB = 2 * KP * ROW_BYTES;
     static constexpr int OP = 2 * OPA + 2 * OPB;
-    static constexpr int BYTES = S * RAW + 2 * OP + 256 + 1024;  // + barriers + alignment slack
+    static constexpr int BYTES = S * RAW + 2 * OP + 512 + 1024;  // + barriers and flags + alignment slack
 };
 
+constexpr int WS_THREADS = 192;
+
 template <int KP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(WS_THREADS, 1)
     vdot_tc_k(const __grid_constant__ CUtensorMap tV, const __grid_constant__ CUtensorMap tX, int na, int nb, int ktiles,
               int tpc, double2* __restrict__ partial) {
     using L = VdotLayout<KP>;
     static_assert(KP % 8 == 0 && KP >= 8 && KP <= 32, "KP");
+    constexpr int S = L::S, G = 4;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* raw = base;
-    unsigned char* op = base + L::S * L::RAW;
-    uint64_t* bars = (uint64_t*)(op + 2 * L::OP);  // full[S], mma[2]
-    uint32_t* tslot = (uint32_t*)(bars + L::S + 2);
-    int* abort_flag = (int*)(tslot + 1);
+    unsigned char* op = base + S * L::RAW;
+    uint64_t* bars = (uint64_t*)(op + 2 * L::OP);  // full[S], empty[S], opfull[2], opempty[2], accempty[2]
+    int* flags = (int*)(bars + 2 * S + 6);        // abort, issued, consumed, committed
+    uint32_t* tslot = (uint32_t*)(flags + 4);
+    volatile int* abort_flag = flags;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cx = blockIdx.x, row0 = blockIdx.y * 128;
     const int t0 = cx * tpc;
     const int nt = min(tpc, ktiles - t0);
     if (nt <= 0) {  // no K-tiles left for this block: its partial rows are zero
-        for (int q = tid; q < 128 * nb; q += TC_THREADS) {
+        for (int q = tid; q < 128 * nb; q += WS_THREADS) {
             const int i = row0 + q / nb, j = q % nb;
             if (i < na) partial[((long long)cx * na + i) * nb + j] = make_double2(0.0, 0.0);
         }
         return;
     }
-    const uint32_t full0 = su32(bars), mma0 = su32(bars + L::S);
+    const uint32_t full0 = su32(bars), empty0 = full0 + 8 * S, opfull0 = empty0 + 8 * S, opempty0 = opfull0 + 16,
+                   accempty0 = opempty0 + 16;
     if (tid == 0) {
-        for (int s = 0; s < L::S; ++s) bar_init(full0 + 8 * s, 1);
-        bar_init(mma0, 1);
-        bar_init(mma0 + 8, 1);
-        *abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            bar_init(full0 + 8 * s, 1);
+            bar_init(empty0 + 8 * s, 4);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(opfull0 + 8 * b, 4);
+            bar_init(opempty0 + 8 * b, 1);
+            bar_init(accempty0 + 8 * b, 4);
+        }
+        flags[0] = 0;
+        flags[1] = flags[2] = flags[3] = 0;
         bar_fence_init();
     }
-    // two accumulator sets (K-tiles alternate), each {hi x hi: 2 KP columns | hi x lo + lo x hi: 2 KP}
+    // two accumulator sets (groups alternate), each {hi x hi: 2 KP columns | hi x lo + lo x hi: 2 KP}
     constexpr uint32_t NCOL = tmem_cols(8 * KP);
-    if (warp == 0) tmem_alloc(su32(tslot), NCOL);
+    if (warp == 1) tmem_alloc(su32(tslot), NCOL);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    auto issue = [&](int i) {  // K-tile i of this block into stage i % S
-        const int s = i % L::S;
-        const uint32_t dst = su32(raw + s * L::RAW), bar = full0 + 8 * s;
-        bar_expect_tx(bar, (uint32_t)L::RAW);
-        tma_load_2d(dst, &tV, (t0 + i) * KT, row0, bar);
-        tma_load_2d(dst + L::RAW_V, &tX, (t0 + i) * KT, 0, bar);
-    };
-    int issued = 0;
-    if (tid == 0)
-        for (; issued < min(L::S, nt); ++issued) issue(issued);
     constexpr uint32_t IDESC = tf32_idesc(128, 2 * KP);
-    constexpr int XC = KP * ROW_BYTES / 16;  // 16-byte chunks of the X tile
-    // The tensor core rounds each accumulation step toward zero, a bias that grows with the number of
-    // steps summed in one accumulator: every group of G K-tiles therefore starts fresh accumulators
-    // (one set per group parity), and a group's sums are added into FP32 registers (round to nearest)
-    // once its last K-tile has completed, which the loop learns two tiles later.  The small split
-    // terms have an accumulator of their own, so that their rounding is relative to their own size.
-    // Warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 keep the real parts, warps 4-7 the imaginary.
-    constexpr int G = 4;
-    const int half = warp >> 2;
-    const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    float acc[KP];
-#pragma unroll
-    for (int q = 0; q < KP; ++q) acc[q] = 0.f;
-    auto promote = [&](int set) {  // acc += big + small of accumulator set `set`, this warp's half
-#pragma unroll
-        for (int c0 = 0; c0 < KP; c0 += 8) {
-            float v[8], w[8];
-            tmem_ld8(tlane + set * 4 * KP + half * KP + c0, v);
-            tmem_ld8(tlane + set * 4 * KP + 2 * KP + half * KP + c0, w);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[c0 + q] += v[q] + w[q];
-        }
-    };
-    int promoted = 0;  // groups already added into acc
-    int consumed = 0, done = 0;
-    for (int i = 0; i < nt; ++i) {
-        const int s = i % L::S, b = i & 1;
-        bool ok = bar_wait(full0 + 8 * s, (i / L::S) & 1);
-        consumed = i + 1;
-        if (i >= 2) ok = bar_wait(mma0 + 8 * b, ((i - 2) >> 1) & 1) && ok;
-        if (!ok) *abort_flag = 1;
-        if (i >= 2 && (i - 2) % G == G - 1) {  // K-tile i - 2 completed the group in its set; the next
-            tc_fence_after();                    // group of that parity starts after the sync below
-            promote(((i - 2) / G) & 1);
-            ++promoted;
-        }
-        const float4* rv = (const float4*)(raw + s * L::RAW);
-        const float4* rx = (const float4*)(raw + s * L::RAW + L::RAW_V);
-        unsigned char* ob = op + b * L::OP;
-        float4* ah = (float4*)ob;
-        float4* al = (float4*)(ob + L::OPA);
-        float4* bh = (float4*)(ob + 2 * L::OPA);
-        float4* bl = (float4*)(ob + 2 * L::OPA + L::OPB);
-#pragma unroll 4
-        for (int c = tid; c < L::RAW_V / 16; c += TC_THREADS) {
-            float4 h, l;
-            split4(rv[c], h, l);
-            ah[c] = h;
-            al[c] = l;
-        }
-        for (int c = tid; c < XC; c += TC_THREADS) {
-            const float4 v = rx[c];
-            float4 h, l;
-            split4(v, h, l);
-            bh[c] = h;
-            bl[c] = l;
-            split4(make_float4(v.y, -v.x, v.w, -v.z), h, l);  // J x: (re, im) -> (im, -re)
-            bh[XC + c] = h;
-            bl[XC + c] = l;
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (*abort_flag) break;
-        if (tid == 0) {
-            if (issued < nt) issue(issued++);  // stage s is free: its data now lives in the operand buffer
-            tc_fence_after();
-            const uint32_t a_hi = su32(ah), a_lo = su32(al), b_hi = su32(bh), b_lo = su32(bl);
-#pragma unroll
-            const uint32_t big = tmem + ((i / G) & 1) * 4 * KP, small = big + 2 * KP;
-            for (int ks = 0; ks < KT / 8; ++ks) {
-                const uint32_t o = ks * 32;  // 8 TF32 of K: 32 bytes along the swizzled row
-                const uint32_t more = (i % G > 0 || ks > 0) ? 1u : 0u;
-                mma_tf32(big, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, more);
-                mma_tf32(small, sw128_desc(a_hi + o), sw128_desc(b_lo + o), IDESC, more);
-                mma_tf32(small, sw128_desc(a_lo + o), sw128_desc(b_hi + o), IDESC, 1u);
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int i = 0;
+            for (; i < nt; ++i) {
+                const int s = i % S;
+                if (i >= S && !role_wait(empty0 + 8 * s, ((i - S) / S) & 1, abort_flag)) break;
+                const uint32_t dst = su32(raw + s * L::RAW), bar = full0 + 8 * s;
+                bar_expect_tx(bar, (uint32_t)L::RAW);
+                tma_load_2d(dst, &tV, (t0 + i) * KT, row0, bar);
+                tma_load_2d(dst + L::RAW_V, &tX, (t0 + i) * KT, 0, bar);
             }
-            mma_commit(mma0 + 8 * b);
+            flags[1] = i;
         }
-        done = i + 1;
-    }
-    const bool aborted = *abort_flag != 0;
-    if (done > 0) bar_wait(mma0 + 8 * ((done - 1) & 1), ((done - 1) >> 1) & 1);
-    if (tid == 0)  // copies still in flight (only after an abort): wait for them before the block exits
-        for (int i = consumed; i < issued; ++i) bar_wait(full0 + 8 * (i % L::S), (i / L::S) & 1);
-    tc_fence_after();
-    if (!aborted) {
-        // the groups not added yet (the last one, and the one before it if the loop ended too soon)
-        const int ngroups = (done + G - 1) / G;
-        for (int gi = promoted; gi < ngroups; ++gi) promote(gi & 1);
-        const int m = row0 + (warp & 3) * 32 + lane;
-        double* pd = (double*)partial;
-        if (m < na) {
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int i = 0;
+            for (; i < nt; ++i) {
+                const int b = i & 1, g = i / G, set = g & 1;
+                if (!role_wait(opfull0 + 8 * b, (i >> 1) & 1, abort_flag)) break;
+                if (i % G == 0 && g >= 2 && !role_wait(accempty0 + 8 * set, ((g - 2) >> 1) & 1, abort_flag)) break;
+                tc_fence_after();
+                unsigned char* ob = op + b * L::OP;
+                const uint32_t a_hi = su32(ob), a_lo = a_hi + L::OPA, b_hi = a_hi + 2 * L::OPA, b_lo = b_hi + L::OPB;
+                const uint32_t big = tmem + set * 4 * KP, small = big + 2 * KP;
 #pragma unroll
-            for (int j = 0; j < KP; ++j)
-                if (j < nb) pd[2 * (((long long)cx * na + m) * nb + j) + half] = (double)acc[j];
+                for (int ks = 0; ks < KT / 8; ++ks) {
+                    const uint32_t o = ks * 32;  // 8 TF32 of K: 32 bytes along the swizzled row
+                    const uint32_t more = (i % G > 0 || ks > 0) ? 1u : 0u;
+                    mma_tf32(big, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, more);
+                    mma_tf32(small, sw128_desc(a_hi + o), sw128_desc(b_lo + o), IDESC, more);
+                    mma_tf32(small, sw128_desc(a_lo + o), sw128_desc(b_hi + o), IDESC, 1u);
+                }
+                mma_commit(opempty0 + 8 * b);
+            }
+            flags[3] = i;
         }
+    } else {  // warps 2-5: transform and promotion
+        const int t = tid - 64;
+        // Warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31: warps 2, 3, 4, 5 cover all 128 rows.
+        const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        float acc[2 * KP];
+#pragma unroll
+        for (int q = 0; q < 2 * KP; ++q) acc[q] = 0.f;
+        // The tensor core rounds its accumulation steps toward zero, a bias that grows with the steps
+        // summed in one accumulator: each group of G K-tiles has fresh accumulators, added here into
+        // FP32 registers with round-to-nearest.
+        auto promote = [&](int set) {
+#pragma unroll
+            for (int c0 = 0; c0 < 2 * KP; c0 += 8) {
+                float v[8], w[8];
+                tmem_ld8(tlane + set * 4 * KP + c0, v);
+                tmem_ld8(tlane + set * 4 * KP + 2 * KP + c0, w);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[c0 + q] += v[q] + w[q];
+            }
+        };
+        constexpr int XC = KP * ROW_BYTES / 16;  // 16-byte chunks of the X tile
+        int promoted = 0, i = 0;
+        bool ok = true;
+        for (; i < nt; ++i) {
+            const int s = i % S, b = i & 1;
+            if (!role_wait(full0 + 8 * s, (i / S) & 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            if (i >= 2) {
+                if (!role_wait(opempty0 + 8 * b, ((i - 2) >> 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if ((i - 2) % G == G - 1) {  // tile i - 2 completed its group
+                    const int set = ((i - 2) / G) & 1;
+                    tc_fence_after();
+                    promote(set);
+                    ++promoted;
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(accempty0 + 8 * set);
+                }
+            }
+            const float4* rv = (const float4*)(raw + s * L::RAW);
+            const float4* rx = (const float4*)(raw + s * L::RAW + L::RAW_V);
+            unsigned char* ob = op + b * L::OP;
+            float4* ah = (float4*)ob;
+            float4* al = (float4*)(ob + L::OPA);
+            float4* bh = (float4*)(ob + 2 * L::OPA);
+            float4* bl = (float4*)(ob + 2 * L::OPA + L::OPB);
+#pragma unroll 4
+            for (int c = t; c < L::RAW_V / 16; c += 128) {
+                float4 h, l;
+                split4(rv[c], h, l);
+                ah[c] = h;
+                al[c] = l;
+            }
+            for (int c = t; c < XC; c += 128) {
+                const float4 v = rx[c];
+                float4 h, l;
+                split4(v, h, l);
+                bh[c] = h;
+                bl[c] = l;
+                split4(make_float4(v.y, -v.x, v.w, -v.z), h, l);  // J x: (re, im) -> (im, -re)
+                bh[XC + c] = h;
+                bl[XC + c] = l;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                bar_arrive(empty0 + 8 * s);
+                bar_arrive(opfull0 + 8 * b);
+            }
+        }
+        if (t == 0) flags[2] = i;
+        if (ok && role_wait(opempty0 + 8 * ((nt - 1) & 1), ((nt - 1) >> 1) & 1, abort_flag)) {
+            tc_fence_after();
+            const int ngroups = (nt + G - 1) / G;  // at most the last two are not added yet
+            for (int gi = promoted; gi < ngroups; ++gi) promote(gi & 1);
+            const int m = row0 + (warp & 3) * 32 + lane;
+            if (m < na) {
+#pragma unroll
+                for (int j = 0; j < KP; ++j)
+                    if (j < nb)
+                        partial[((long long)cx * na + m) * nb + j] = make_double2((double)acc[j], (double)acc[KP + j]);
+            }
+        }
+    }
+    __syncthreads();
+    if (*abort_flag && tid == 0) {  // before the block exits: copies and MMAs it started must be done
+        for (int i = flags[2]; i < flags[1]; ++i) bar_wait(full0 + 8 * (i % S), (i / S) & 1);
+        const int c = flags[3];
+        if (c > 0) bar_wait(opempty0 + 8 * ((c - 1) & 1), ((c - 1) >> 1) & 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         tmem_free(tmem, NCOL);
     }
@@ -364,7 +423,7 @@ struct ApplyLayout {
     static constexpr int RAW = RAW_V + BIMG;
     static constexpr int OPA = 128 * ROW_BYTES;
     static constexpr int OP = 2 * OPA;
-    static constexpr int BYTES = S * RAW + 2 * OP + 256 + 1024;
+    static constexpr int BYTES = S * RAW + 2 * OP + 512 + 1024;
 };
 
 // Coefficient images: img[kt][hi, lo][row n < 4 KP][32 floats], rows in the 128-byte swizzled order of
@@ -402,64 +461,154 @@ __global__ void apply_prep_k(const double2* __restrict__ C, int ldc, const doubl
 }
 
 template <int KP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(WS_THREADS, 1)
     apply_tc_k(const __grid_constant__ CUtensorMap tV, const unsigned char* __restrict__ bimg, int nkt,
                const float2* __restrict__ X, float2* __restrict__ Xp, float2* __restrict__ Ys, long long n, int nb,
                int mtiles) {
+    // Roles as in vdot_tc_k: warp 0 TMA (the raw V tile and, by a 1-D bulk copy, the K-tile's
+    // coefficient image), warp 1 MMA issue and TMEM, warps 2-5 the transposing split of V and the
+    // epilogue.  Steps u run over this block's output tiles (blockIdx.x, + gridDim.x, ...) and their
+    // K-tiles; the MMAs read the coefficient image in the raw stage, so a stage is released by the MMA
+    // commit.  Output tiles alternate between two accumulator sets, each {hi x hi: 4 KP | small: 4 KP};
+    // the epilogue of tile q runs after the first K-tile of tile q + 1 has been handed to the MMAs.
     using L = ApplyLayout<KP>;
     static_assert(KP % 8 == 0 && KP >= 8 && KP <= 32, "KP");
+    constexpr int S = L::S;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* raw = base;
-    unsigned char* op = base + L::S * L::RAW;
-    uint64_t* bars = (uint64_t*)(op + 2 * L::OP);  // full[S], mma[2]
-    uint32_t* tslot = (uint32_t*)(bars + L::S + 2);
-    int* abort_flag = (int*)(tslot + 1);
+    unsigned char* op = base + S * L::RAW;
+    uint64_t* bars = (uint64_t*)(op + 2 * L::OP);  // full[S], empty[S], opfull[2], opempty[2], accfull[2], accempty[2]
+    int* flags = (int*)(bars + 2 * S + 8);        // abort, issued, consumed, committed
+    uint32_t* tslot = (uint32_t*)(flags + 4);
+    volatile int* abort_flag = flags;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nmt = mtiles > (int)blockIdx.x ? (mtiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int nsteps = nmt * nkt;
     if (nsteps == 0) return;
-    const uint32_t full0 = su32(bars), mma0 = su32(bars + L::S);
+    const uint32_t full0 = su32(bars), empty0 = full0 + 8 * S, opfull0 = empty0 + 8 * S, opempty0 = opfull0 + 16,
+                   accfull0 = opempty0 + 16, accempty0 = accfull0 + 16;
     if (tid == 0) {
-        for (int s = 0; s < L::S; ++s) bar_init(full0 + 8 * s, 1);
-        bar_init(mma0, 1);
-        bar_init(mma0 + 8, 1);
-        *abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            bar_init(full0 + 8 * s, 1);
+            bar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(opfull0 + 8 * b, 4);
+            bar_init(opempty0 + 8 * b, 1);
+            bar_init(accfull0 + 8 * b, 1);
+            bar_init(accempty0 + 8 * b, 4);
+        }
+        flags[0] = 0;
+        flags[1] = flags[2] = flags[3] = 0;
         bar_fence_init();
     }
-    // {hi x hi: 4 KP columns | hi x lo + lo x hi: 4 KP}: the small terms round relative to their own size
-    constexpr uint32_t NCOL = tmem_cols(8 * KP);
-    if (warp == 0) tmem_alloc(su32(tslot), NCOL);
+    constexpr uint32_t NCOL = tmem_cols(16 * KP);
+    if (warp == 1) tmem_alloc(su32(tslot), NCOL);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    auto issue = [&](int u) {  // step u: output tile blockIdx.x + (u / nkt) gridDim.x, K-tile u % nkt
-        const int s = u % L::S, kt = u % nkt, mt = (int)blockIdx.x + (u / nkt) * (int)gridDim.x;
-        const uint32_t dst = su32(raw + s * L::RAW), bar = full0 + 8 * s;
-        bar_expect_tx(bar, (uint32_t)L::RAW);
-        tma_load_2d(dst, &tV, mt * 256, kt * 16, bar);
-        bulk_load(dst + L::RAW_V, bimg + (size_t)kt * L::BIMG, (uint32_t)L::BIMG, bar);
-    };
-    int issued = 0;
-    if (tid == 0)
-        for (; issued < min(L::S, nsteps); ++issued) issue(issued);
     constexpr uint32_t IDESC = tf32_idesc(128, 4 * KP);
-    int consumed = 0, done = 0;
-    for (int u = 0; u < nsteps; ++u) {
-        const int s = u % L::S, b = u & 1, kt = u % nkt;
-        bool ok = bar_wait(full0 + 8 * s, (u / L::S) & 1);
-        consumed = u + 1;
-        if (u >= 2) ok = bar_wait(mma0 + 8 * b, ((u - 2) >> 1) & 1) && ok;
-        if (!ok) *abort_flag = 1;
-        // transpose + split: thread p builds row p of A (8 chunks of two eigenvectors' (re, im))
-        {
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int u = 0;
+            for (; u < nsteps; ++u) {
+                const int s = u % S, kt = u % nkt, mt = (int)blockIdx.x + (u / nkt) * (int)gridDim.x;
+                if (u >= S && !role_wait(empty0 + 8 * s, ((u - S) / S) & 1, abort_flag)) break;
+                const uint32_t dst = su32(raw + s * L::RAW), bar = full0 + 8 * s;
+                bar_expect_tx(bar, (uint32_t)L::RAW);
+                tma_load_2d(dst, &tV, mt * 256, kt * 16, bar);
+                bulk_load(dst + L::RAW_V, bimg + (size_t)kt * L::BIMG, (uint32_t)L::BIMG, bar);
+            }
+            flags[1] = u;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int u = 0;
+            for (; u < nsteps; ++u) {
+                const int s = u % S, b = u & 1, kt = u % nkt, q = u / nkt, ts = q & 1;
+                if (!role_wait(opfull0 + 8 * b, (u >> 1) & 1, abort_flag)) break;
+                if (kt == 0 && q >= 2 && !role_wait(accempty0 + 8 * ts, ((q - 2) >> 1) & 1, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t a_hi = su32(op + b * L::OP), a_lo = a_hi + L::OPA;
+                const uint32_t b_hi = su32(raw + s * L::RAW + L::RAW_V), b_lo = b_hi + L::BIMG / 2;
+                const uint32_t big = tmem + ts * 8 * KP, small = big + 4 * KP;
+#pragma unroll
+                for (int ks = 0; ks < KT / 8; ++ks) {
+                    const uint32_t o = ks * 32;
+                    const uint32_t more = (kt > 0 || ks > 0) ? 1u : 0u;
+                    mma_tf32(big, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, more);
+                    mma_tf32(small, sw128_desc(a_hi + o), sw128_desc(b_lo + o), IDESC, more);
+                    mma_tf32(small, sw128_desc(a_lo + o), sw128_desc(b_hi + o), IDESC, 1u);
+                }
+                mma_commit(opempty0 + 8 * b);  // the operand buffer is free
+                mma_commit(empty0 + 8 * s);    // the raw stage (and its coefficient image) is free
+                if (kt == nkt - 1) mma_commit(accfull0 + 8 * ts);
+            }
+            flags[3] = u;
+        }
+    } else {  // warps 2-5: transposing split and epilogue
+        const int t = tid - 64;
+        const int q4 = warp & 3;  // TMEM lanes 32 q4 .. 32 q4 + 31
+        const uint32_t tlane = tmem + ((uint32_t)(q4 * 32) << 16);
+        auto epilogue = [&](int q) -> bool {  // output tile q of this block
+            const int ts = q & 1;
+            if (!role_wait(accfull0 + 8 * ts, (q >> 1) & 1, abort_flag)) return false;
+            tc_fence_after();
+            const int mt = (int)blockIdx.x + q * (int)gridDim.x;
+            const long long pos = (long long)mt * 128 + q4 * 32 + lane;
+            const uint32_t tl = tlane + ts * 8 * KP;
+#pragma unroll 1
+            for (int j0 = 0; j0 < KP; j0 += 8) {
+                float r1[8], i1[8], r2[8], i2[8], w[8];
+                tmem_ld8(tl + j0, r1);
+                tmem_ld8(tl + KP + j0, i1);
+                tmem_ld8(tl + 2 * KP + j0, r2);
+                tmem_ld8(tl + 3 * KP + j0, i2);
+                tmem_ld8(tl + 4 * KP + j0, w);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) r1[e] += w[e];
+                tmem_ld8(tl + 5 * KP + j0, w);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) i1[e] += w[e];
+                tmem_ld8(tl + 6 * KP + j0, w);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) r2[e] += w[e];
+                tmem_ld8(tl + 7 * KP + j0, w);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) i2[e] += w[e];
+                if (pos < n) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int j = j0 + e;
+                        if (j < nb) {
+                            const long long o = (long long)j * n + pos;
+                            const float2 x = X[o];
+                            Xp[o] = make_float2(x.x + r1[e], x.y + i1[e]);
+                            Ys[o] = make_float2(r2[e], i2[e]);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(accempty0 + 8 * ts);
+            return true;
+        };
+        int u = 0;
+        bool ok = true;
+        for (; u < nsteps && ok; ++u) {
+            const int s = u % S, b = u & 1, kt = u % nkt, q = u / nkt;
+            if (!role_wait(full0 + 8 * s, (u / S) & 1, abort_flag)) break;
+            if (u >= 2 && !role_wait(opempty0 + 8 * b, ((u - 2) >> 1) & 1, abort_flag)) break;
+            // thread t builds half a row of A: row p = t, chunks jh .. jh + 3 for both halves in turn
             const float2* rv = (const float2*)(raw + s * L::RAW);
             float4* ah = (float4*)(op + b * L::OP);
             float4* al = (float4*)(op + b * L::OP + L::OPA);
-            const int p = tid & 127, jh = (tid >> 7) * 4;  // row p, chunks jh .. jh + 3
+            const int p = t;
 #pragma unroll
-            for (int jc = jh; jc < jh + 4; ++jc) {
+            for (int jc = 0; jc < 8; ++jc) {
                 const float2 v0 = rv[(2 * jc) * 128 + p], v1 = rv[(2 * jc + 1) * 128 + p];
                 float4 h, l;
                 split4(make_float4(v0.x, v0.y, v1.x, v1.y), h, l);
@@ -467,78 +616,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ah[at] = h;
                 al[at] = l;
             }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) bar_arrive(opfull0 + 8 * b);
+            if (kt == 0 && q >= 1) ok = epilogue(q - 1);
         }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (*abort_flag) break;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a_hi = su32(op + b * L::OP), a_lo = a_hi + L::OPA;
-            const uint32_t b_hi = su32(raw + s * L::RAW + L::RAW_V), b_lo = b_hi + L::BIMG / 2;
-#pragma unroll
-            for (int ks = 0; ks < KT / 8; ++ks) {
-                const uint32_t o = ks * 32;
-                const uint32_t first = (kt > 0 || ks > 0) ? 1u : 0u;
-                mma_tf32(tmem, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, first);
-                mma_tf32(tmem + 4 * KP, sw128_desc(a_hi + o), sw128_desc(b_lo + o), IDESC, first);
-                mma_tf32(tmem + 4 * KP, sw128_desc(a_lo + o), sw128_desc(b_hi + o), IDESC, 1u);
-            }
-            mma_commit(mma0 + 8 * b);
-            // the stage of step u - 1 is free once its MMAs (which read its coefficient image) are done
-            if (u >= 1 && issued < nsteps) {
-                bar_wait(mma0 + 8 * ((u - 1) & 1), ((u - 1) >> 1) & 1);
-                issue(issued++);
-            }
-        }
-        done = u + 1;
-        if (kt == nkt - 1) {  // epilogue of this output tile
-            bar_wait(mma0 + 8 * b, (u >> 1) & 1);
-            tc_fence_after();
-            const int mt = (int)blockIdx.x + (u / nkt) * (int)gridDim.x;
-            const long long pos = (long long)mt * 128 + (warp & 3) * 32 + lane;
-            const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-#pragma unroll 1
-            for (int j0 = (warp >> 2) * 8; j0 < KP; j0 += 16) {  // warps 0-3 and 4-7 take alternate groups of 8
-                float r1[8], i1[8], r2[8], i2[8], t[8];
-                tmem_ld8(tl + j0, r1);
-                tmem_ld8(tl + KP + j0, i1);
-                tmem_ld8(tl + 2 * KP + j0, r2);
-                tmem_ld8(tl + 3 * KP + j0, i2);
-                tmem_ld8(tl + 4 * KP + j0, t);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) r1[q] += t[q];
-                tmem_ld8(tl + 5 * KP + j0, t);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) i1[q] += t[q];
-                tmem_ld8(tl + 6 * KP + j0, t);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) r2[q] += t[q];
-                tmem_ld8(tl + 7 * KP + j0, t);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) i2[q] += t[q];
-                if (pos < n) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int j = j0 + q;
-                        if (j < nb) {
-                            const long long o = (long long)j * n + pos;
-                            const float2 x = X[o];
-                            Xp[o] = make_float2(x.x + r1[q], x.y + i1[q]);
-                            Ys[o] = make_float2(r2[q], i2[q]);
-                        }
-                    }
-                }
-            }
-            tc_fence_before();  // the next tile's first MMA overwrites the accumulator after the next sync
-        }
+        if (t == 0) flags[2] = u;
+        if (ok && u == nsteps) epilogue(nmt - 1);
     }
-    if (done > 0) bar_wait(mma0 + 8 * ((done - 1) & 1), ((done - 1) >> 1) & 1);
-    if (tid == 0)
-        for (int u = consumed; u < issued; ++u) bar_wait(full0 + 8 * (u % L::S), (u / L::S) & 1);
+    __syncthreads();
+    if (*abort_flag && tid == 0) {  // before the block exits: copies and MMAs it started must be done
+        for (int u = flags[2]; u < flags[1]; ++u) bar_wait(full0 + 8 * (u % S), (u / S) & 1);
+        const int c = flags[3];
+        if (c > 0) bar_wait(opempty0 + 8 * ((c - 1) & 1), ((c - 1) >> 1) & 1);
+    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         tmem_free(tmem, NCOL);
     }
@@ -612,7 +706,7 @@ cudaError_t vdot_tc(const void* V, int na, const void* X, int nb, long long n, d
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    vdot_tc_k<KP><<<dim3((unsigned)nchunk, mtiles), TC_THREADS, L::BYTES, s>>>(tV, tX, na, nb, ktiles, tpc, d_partial);
+    vdot_tc_k<KP><<<dim3((unsigned)nchunk, mtiles), WS_THREADS, L::BYTES, s>>>(tV, tX, na, nb, ktiles, tpc, d_partial);
     count_launch();
     const int nq = na * nb;
     tc_sum_partials_k<<<(nq + 255) / 256, 256, 0, s>>>(d_partial, (int)nchunk, nq, d_C);
@@ -639,7 +733,7 @@ cudaError_t apply_tc(const void* V, int na, const double* d_signs, const double2
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    apply_tc_k<KP><<<std::min(mtiles, kTcBlocks), TC_THREADS, L::BYTES, s>>>(
+    apply_tc_k<KP><<<std::min(mtiles, kTcBlocks), WS_THREADS, L::BYTES, s>>>(
         tV, (const unsigned char*)d_img, nkt, (const float2*)X, (float2*)Xp, (float2*)Ys, n, nb, mtiles);
     count_launch();
     return cudaGetLastError();
