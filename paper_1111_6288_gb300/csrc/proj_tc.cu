@@ -15,9 +15,9 @@
 //
 // Data path, one warp-specialised block per SM: a producer warp brings raw FP32 tiles of V and X into
 // shared memory by TMA (cp.async.bulk.tensor, this GPU's memory, no multicast) through a multi-stage
-// mbarrier pipeline; four warps split each tile into the hi/lo operand tiles (128-byte swizzled,
+// mbarrier pipeline; eight warps split each tile into the hi/lo operand tiles (128-byte swizzled,
 // K-major: one 128-byte row of 32 floats per matrix row); one thread issues tcgen05.mma (kind::tf32,
-// M = 128, cta_group::1) into TMEM accumulators, which the four warps read back with tcgen05.ld.
+// M = 128, cta_group::1) into TMEM accumulators, which the eight warps read back with tcgen05.ld.
 // Every wait on a barrier is bounded (about a second); a wait that runs out records the timeout in
 // g_tc_timeouts and makes every role of the block stop; the block then waits (bounded) for the copies
 // and MMAs it started and frees its TMEM before it returns.
@@ -183,14 +183,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 //            V rows [128 my, 128 my + 128) (rows beyond na arrive as zeros) and the KP rows of X;
 //   warp 1   MMA issuer (and TMEM owner): D = V [X; J X]^T, M = 128, N = 2 KP, three TF32 products
 //            per K-step, into the accumulator set of the tile's group of G K-tiles;
-//   warps 2-5  split each raw tile into the hi/lo operand tiles (the 128-byte swizzle keeps every
+//   warps 2-9  split each raw tile into the hi/lo operand tiles (the 128-byte swizzle keeps every
 //            16-byte chunk at its offset, J X too, rows KP..2KP-1), and add each completed group's
 //            accumulators into FP32 registers; at the end they write partial[cx][i][j] = (Re, Im).
-// Barriers: full[s] (TMA bytes), empty[s] (the four transform warps), opfull[b] (transform warps),
+// Barriers: full[s] (TMA bytes), empty[s] (the eight transform warps), opfull[b] (transform warps),
 // opempty[b] (MMA commit), accempty[set] (transform warps, once a group's sums are read).
 template <int KP>
 struct VdotLayout {
-    static constexpr int S = 4;
+    static constexpr int S = 6;
     static constexpr int RAW_V = 128 * ROW_BYTES;
     static constexpr int RAW_X = KP * ROW_BYTES;
     static constexpr int RAW = RAW_V + RAW_X;
@@ -200,7 +200,12 @@ struct VdotLayout {
     static constexpr int BYTES = S * RAW + 2 * OP + 512 + 1024;  // + barriers and flags + alignment slack
 };
 
-constexpr int WS_THREADS = 192;
+// Warp 0 TMA, warp 1 MMA and TMEM, warps 2-9 transform (two warps per scheduler hide each other's
+// shared-memory and conversion latency); warps w and w + 4 share TMEM lanes 32 (w % 4) .. and split the
+// accumulator columns.
+constexpr int WS_THREADS = 320;
+constexpr int NXW = 8;                 // transform warps
+constexpr int NXT = NXW * 32;          // transform threads
 
 template <int KP>
 __global__ void __launch_bounds__(WS_THREADS, 1)
@@ -233,12 +238,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             bar_init(full0 + 8 * s, 1);
-            bar_init(empty0 + 8 * s, 4);
+            bar_init(empty0 + 8 * s, NXW);
         }
         for (int b = 0; b < 2; ++b) {
-            bar_init(opfull0 + 8 * b, 4);
+            bar_init(opfull0 + 8 * b, NXW);
             bar_init(opempty0 + 8 * b, 1);
-            bar_init(accempty0 + 8 * b, 4);
+            bar_init(accempty0 + 8 * b, NXW);
         }
         flags[0] = 0;
         flags[1] = flags[2] = flags[3] = 0;
@@ -288,22 +293,24 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             }
             flags[3] = i;
         }
-    } else {  // warps 2-5: transform and promotion
+    } else {  // warps 2-9: transform and promotion
         const int t = tid - 64;
-        // Warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31: warps 2, 3, 4, 5 cover all 128 rows.
+        // Warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31; of the two warps on a quarter, the first
+        // keeps the real parts (columns j), the second the imaginary parts (KP + j).
+        const int half = (warp - 2) >> 2;
         const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        float acc[2 * KP];
+        float acc[KP];
 #pragma unroll
-        for (int q = 0; q < 2 * KP; ++q) acc[q] = 0.f;
+        for (int q = 0; q < KP; ++q) acc[q] = 0.f;
         // The tensor core rounds its accumulation steps toward zero, a bias that grows with the steps
         // summed in one accumulator: each group of G K-tiles has fresh accumulators, added here into
         // FP32 registers with round-to-nearest.
         auto promote = [&](int set) {
 #pragma unroll
-            for (int c0 = 0; c0 < 2 * KP; c0 += 8) {
+            for (int c0 = 0; c0 < KP; c0 += 8) {
                 float v[8], w[8];
-                tmem_ld8(tlane + set * 4 * KP + c0, v);
-                tmem_ld8(tlane + set * 4 * KP + 2 * KP + c0, w);
+                tmem_ld8(tlane + set * 4 * KP + half * KP + c0, v);
+                tmem_ld8(tlane + set * 4 * KP + 2 * KP + half * KP + c0, w);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[c0 + q] += v[q] + w[q];
             }
@@ -340,13 +347,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             float4* bh = (float4*)(ob + 2 * L::OPA);
             float4* bl = (float4*)(ob + 2 * L::OPA + L::OPB);
 #pragma unroll 4
-            for (int c = t; c < L::RAW_V / 16; c += 128) {
+            for (int c = t; c < L::RAW_V / 16; c += NXT) {
                 float4 h, l;
                 split4(rv[c], h, l);
                 ah[c] = h;
                 al[c] = l;
             }
-            for (int c = t; c < XC; c += 128) {
+            for (int c = t; c < XC; c += NXT) {
                 const float4 v = rx[c];
                 float4 h, l;
                 split4(v, h, l);
@@ -369,11 +376,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             const int ngroups = (nt + G - 1) / G;  // at most the last two are not added yet
             for (int gi = promoted; gi < ngroups; ++gi) promote(gi & 1);
             const int m = row0 + (warp & 3) * 32 + lane;
+            double* pd = (double*)partial;
             if (m < na) {
 #pragma unroll
                 for (int j = 0; j < KP; ++j)
-                    if (j < nb)
-                        partial[((long long)cx * na + m) * nb + j] = make_double2((double)acc[j], (double)acc[KP + j]);
+                    if (j < nb) pd[2 * (((long long)cx * na + m) * nb + j) + half] = (double)acc[j];
             }
         }
     }
@@ -417,7 +424,7 @@ __global__ void tc_sum_partials_k(const double2* __restrict__ partial, int nchun
 // reads the accumulator and writes X_perp and Y_s while the next tiles' copies are in flight.
 template <int KP>
 struct ApplyLayout {
-    static constexpr int S = 3;
+    static constexpr int S = KP <= 16 ? 5 : (KP <= 24 ? 4 : 3);
     static constexpr int RAW_V = 16 * 256 * 4;        // 16 eigenvectors x 128 complex positions
     static constexpr int BIMG = 2 * 4 * KP * ROW_BYTES;  // hi and lo images of the 4 KP coefficient rows
     static constexpr int RAW = RAW_V + BIMG;
@@ -466,7 +473,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                const float2* __restrict__ X, float2* __restrict__ Xp, float2* __restrict__ Ys, long long n, int nb,
                int mtiles) {
     // Roles as in vdot_tc_k: warp 0 TMA (the raw V tile and, by a 1-D bulk copy, the K-tile's
-    // coefficient image), warp 1 MMA issue and TMEM, warps 2-5 the transposing split of V and the
+    // coefficient image), warp 1 MMA issue and TMEM, warps 2-9 the transposing split of V and the
     // epilogue.  Steps u run over this block's output tiles (blockIdx.x, + gridDim.x, ...) and their
     // K-tiles; the MMAs read the coefficient image in the raw stage, so a stage is released by the MMA
     // commit.  Output tiles alternate between two accumulator sets, each {hi x hi: 4 KP | small: 4 KP};
@@ -494,10 +501,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             bar_init(empty0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
-            bar_init(opfull0 + 8 * b, 4);
+            bar_init(opfull0 + 8 * b, NXW);
             bar_init(opempty0 + 8 * b, 1);
             bar_init(accfull0 + 8 * b, 1);
-            bar_init(accempty0 + 8 * b, 4);
+            bar_init(accempty0 + 8 * b, NXW);
         }
         flags[0] = 0;
         flags[1] = flags[2] = flags[3] = 0;
@@ -548,7 +555,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             }
             flags[3] = u;
         }
-    } else {  // warps 2-5: transposing split and epilogue
+    } else {  // warps 2-9: transposing split and epilogue
         const int t = tid - 64;
         const int q4 = warp & 3;  // TMEM lanes 32 q4 .. 32 q4 + 31
         const uint32_t tlane = tmem + ((uint32_t)(q4 * 32) << 16);
@@ -560,7 +567,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             const long long pos = (long long)mt * 128 + q4 * 32 + lane;
             const uint32_t tl = tlane + ts * 8 * KP;
 #pragma unroll 1
-            for (int j0 = 0; j0 < KP; j0 += 8) {
+            for (int j0 = 8 * ((warp - 2) >> 2); j0 < KP; j0 += 16) {  // the quarter's two warps alternate
                 float r1[8], i1[8], r2[8], i2[8], w[8];
                 tmem_ld8(tl + j0, r1);
                 tmem_ld8(tl + KP + j0, i1);
@@ -602,13 +609,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             const int s = u % S, b = u & 1, kt = u % nkt, q = u / nkt;
             if (!role_wait(full0 + 8 * s, (u / S) & 1, abort_flag)) break;
             if (u >= 2 && !role_wait(opempty0 + 8 * b, ((u - 2) >> 1) & 1, abort_flag)) break;
-            // thread t builds half a row of A: row p = t, chunks jh .. jh + 3 for both halves in turn
+            // thread t builds half a row of A
             const float2* rv = (const float2*)(raw + s * L::RAW);
             float4* ah = (float4*)(op + b * L::OP);
             float4* al = (float4*)(op + b * L::OP + L::OPA);
-            const int p = t;
+            const int p = t & 127, jh = (t >> 7) * 4;  // row p, chunks jh .. jh + 3
 #pragma unroll
-            for (int jc = 0; jc < 8; ++jc) {
+            for (int jc = jh; jc < jh + 4; ++jc) {
                 const float2 v0 = rv[(2 * jc) * 128 + p], v1 = rv[(2 * jc + 1) * 128 + p];
                 float4 h, l;
                 split4(make_float4(v0.x, v0.y, v1.x, v1.y), h, l);
