@@ -57,7 +57,7 @@ WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV
 # the kernel case (cold caches).  When the kernel source changes the ratios are stale and `traffic`
 # is reported as null until they are measured again.
 KERNEL_SHA = "f7f9e39adeb0aa18"
-DRAM_OVER_ALGORITHMIC = {"f32_16x16x16x32_solve": 0.14, "f32_24x24x24x48": 0.87}
+DRAM_OVER_ALGORITHMIC = {"f32_16x16x16x32_solve": 0.09, "f32_24x24x24x48": 0.87}
 HBM_DIMS = (24, 24, 24, 48)  # the HBM-bound case: links and vectors far beyond the 129 MB L2
 
 
@@ -537,6 +537,54 @@ def batched_case(args):
     print(json.dumps({"batched_case": out}), flush=True)
 
 
+def projection_case(args):
+    """The small-space projection alone (ov_project_small): a bank of --proj-nev FP32 vectors on the
+    lattice --proj-dims and batches of --proj-k vectors (seeded Gaussian, drawn on the device), on the
+    tensor cores (three calls first, the ones a profiler capture skips into) and on the CUDA cores,
+    CUDA-event timed.  Prints one JSON object (a case study, not the bench line)."""
+    import numpy as np
+    import torch
+
+    import paper_1111_6288_gb300 as P
+
+    torch.cuda.set_device(0)
+    dims = tuple(int(v) for v in args.proj_dims.split(","))
+    ks = [int(v) for v in args.proj_k.split(",")]
+    site = tuple(reversed(dims)) + (4, 3)
+    ctx = P.Context(P.Params(dims=dims, eps=SQRT_EPS ** 2, poly_degree=4, precision=P.OV_PREC_F32,
+                             inner_precision=P.OV_PREC_F32, max_nrhs=max(ks)))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    V = torch.randn((args.proj_nev,) + site, dtype=torch.complex64, device="cuda", generator=g)
+    P.deflate(ctx, V, np.linspace(-1.0, 1.0, args.proj_nev))
+    del V
+    out = {"lattice": list(dims), "n_ev": args.proj_nev, "bank_bytes": args.proj_nev * 12 * int(np.prod(dims)) * 8,
+           "runs": {}}
+    for k in ks:
+        x = torch.randn((k,) + site, dtype=torch.complex64, device="cuda", generator=g)
+        ys, xp = torch.empty_like(x), torch.empty_like(x)
+        ms = {}
+        for method, name in ((2, "tensor_cores"), (1, "cuda_cores")):
+            ctx.set_projection(method)
+            for _ in range(3):
+                P.project_small(ctx, x, ys, xp)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                P.project_small(ctx, x, ys, xp)
+            e1.record()
+            torch.cuda.synchronize()
+            ms[name] = e0.elapsed_time(e1) / 3
+        P.sync(ctx)
+        out["runs"][str(k)] = ms
+        print(f"projection_case N {args.proj_nev} k {k}: tensor cores {ms['tensor_cores']:.2f} ms, "
+              f"CUDA cores {ms['cuda_cores']:.2f} ms", flush=True)
+        del x, ys, xp
+    ctx.close()
+    print(json.dumps({"projection_case": out}), flush=True)
+
+
 def precision_case(args):
     """The bench's solve (16^3x32, 50 H_w modes, 32 D_ov low modes per chiral sector, adaptive order,
     minimax n = 527, m = 0.02, one point source, 1e-10) with each inner precision: FP32, FP16- and
@@ -690,6 +738,12 @@ def main():
     ap.add_argument("--batch-phases", type=int, default=2, help="distinct phases q E used (first ones)")
     ap.add_argument("--batch-nev", type=int, default=100, help="eigenvectors of Q per phase")
     ap.add_argument("--batch-inner", default="f32", help="inner precisions of the batched case (f32,f16,bf16)")
+    ap.add_argument("--projection-case", action="store_true",
+                    help="case study: the small-space projection on the tensor cores and on the CUDA cores, then "
+                         "exit without a bench line")
+    ap.add_argument("--proj-dims", default="24,24,24,48", help="lattice of the projection case")
+    ap.add_argument("--proj-nev", type=int, default=100, help="bank size of the projection case")
+    ap.add_argument("--proj-k", default="8,12,24,32", help="batch sizes of the projection case")
     ap.add_argument("--precision-case", action="store_true",
                     help="case study: the bench's solve with FP32, FP16-, BF16-stored and FP64 inner CGs, then "
                          "exit without a bench line")
@@ -718,6 +772,9 @@ def main():
         return
     if args.precision_case:
         precision_case(args)
+        return
+    if args.projection_case:
+        projection_case(args)
         return
     if args.kernel_case:
         kernel_case(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_precision, args.kernel_shape)
