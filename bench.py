@@ -472,6 +472,8 @@ def batched_case(args):
     import synth
 
     torch.cuda.set_device(0)
+    dims = tuple(int(v) for v in args.batch_dims.split(","))
+    degree, sqrt_eps, mass, nsrc = args.batch_degree, args.batch_sqrt_eps, args.batch_mass, args.batch_sources
     fields = [float(v) for v in args.batch_fields.split(",")]
     phases = []
     for E in fields:
@@ -480,14 +482,16 @@ def batched_case(args):
             if ph not in phases:
                 phases.append(ph)
     phases = phases[:args.batch_phases]
-    U = torch.from_numpy(synth.random_su3_field(BATCH_DIMS, LINK_EPS, 0)).cuda()
-    out = {"workload": f"24^3x48 Dirichlet x,t, 12 point sources x {len(phases)} field phases, N_ev {args.batch_nev}, "
-                       f"n {DEGREE} minimax, m {MASS}, tol {TOL}", "phases": phases, "runs": {}}
-    b1 = synth.point_sources(BATCH_DIMS)
+    U = torch.from_numpy(synth.random_su3_field(dims, args.batch_link_eps, 0)).cuda()
+    out = {"workload": f"{dims[0]}^3x{dims[3]} Dirichlet x,t, links exp(i {args.batch_link_eps} H), {nsrc} point sources x "
+                       f"{len(phases)} field phases, N_ev {args.batch_nev}, n {degree} minimax on [{sqrt_eps ** 2:g}, 1], "
+                       f"m {mass}, tol {TOL}", "phases": phases, "runs": {}}
+    sc = [(s, c) for s in range(4) for c in range(3)][:nsrc]
+    b1 = synth.point_sources(dims, sc)
     for inner in args.batch_inner.split(","):
         prec = {"f32": P.OV_PREC_F32, "f16": P.OV_PREC_F16, "bf16": P.OV_PREC_BF16}[inner]
-        nrhs = 12 * len(phases)
-        ctx = P.Context(P.Params(dims=BATCH_DIMS, bc=BATCH_BC, m0=M0, eps=SQRT_EPS ** 2, poly_degree=DEGREE,
+        nrhs = nsrc * len(phases)
+        ctx = P.Context(P.Params(dims=dims, bc=BATCH_BC, m0=M0, eps=sqrt_eps ** 2, poly_degree=degree,
                                  poly_kind=1, precision=prec, inner_precision=prec, max_nrhs=nrhs, adaptive_order=1))
         ctx.set_gauge(U)
         t0 = time.perf_counter()
@@ -500,15 +504,15 @@ def batched_case(args):
             print(f"batched_case {inner}: eigensolver phase {ph:.3e}: {eig[-1]['seconds']:.1f} s", flush=True)
         setup_s = time.perf_counter() - t0
         b = torch.from_numpy(np.concatenate([b1] * len(phases))).cuda()
-        ph_rhs = [ph for ph in phases for _ in range(12)]
+        ph_rhs = [ph for ph in phases for _ in range(nsrc)]
         # single-source reference solves (one per phase; the first also times the launch shapes)
         single = []
-        for ph in phases:
+        for ph in phases[:args.batch_single]:
             bs = b[:1].clone()
             xs = torch.zeros_like(bs)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            st = P.solve_overlap(ctx, bs, xs, MASS, tol=TOL, phase=[ph])
+            st = P.solve_overlap(ctx, bs, xs, mass, tol=TOL, phase=[ph])
             torch.cuda.synchronize()
             single.append({"phase": ph, "seconds": time.perf_counter() - t1, "outer": st.outer_iters,
                            "inner": st.inner_iters, "wilson": st.dslash_calls, "residual": st.true_residual})
@@ -517,12 +521,12 @@ def batched_case(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        st = P.solve_overlap(ctx, b, x, MASS, tol=TOL, phase=ph_rhs)
+        st = P.solve_overlap(ctx, b, x, mass, tol=TOL, phase=ph_rhs)
         e1.record()
         torch.cuda.synchronize()
         secs = e0.elapsed_time(e1) / 1e3
-        applies = st.dslash_calls / (2 * DEGREE + 1)
-        single_per_source = sum(r["seconds"] for r in single) / len(single)
+        applies = st.dslash_calls / (2 * degree + 1)
+        single_per_source = sum(r["seconds"] for r in single) / len(single) if single else float("nan")
         out["runs"][inner] = {
             "setup_s": setup_s, "eigensolver": eig, "batch_seconds": secs, "nrhs": nrhs,
             "seconds_per_source": secs / nrhs, "single_source_seconds": single_per_source,
@@ -738,6 +742,13 @@ def main():
     ap.add_argument("--batch-phases", type=int, default=2, help="distinct phases q E used (first ones)")
     ap.add_argument("--batch-nev", type=int, default=100, help="eigenvectors of Q per phase")
     ap.add_argument("--batch-inner", default="f32", help="inner precisions of the batched case (f32,f16,bf16)")
+    ap.add_argument("--batch-dims", default="24,24,24,48", help="lattice of the batched case")
+    ap.add_argument("--batch-link-eps", type=float, default=LINK_EPS, help="link spread of the batched case")
+    ap.add_argument("--batch-degree", type=int, default=DEGREE, help="polynomial degree of the batched case")
+    ap.add_argument("--batch-sqrt-eps", type=float, default=SQRT_EPS, help="sqrt(eps) of the batched case")
+    ap.add_argument("--batch-mass", type=float, default=MASS, help="quark mass of the batched case")
+    ap.add_argument("--batch-sources", type=int, default=12, help="spin-colour point sources per field phase")
+    ap.add_argument("--batch-single", type=int, default=2, help="phases with a single-source reference solve")
     ap.add_argument("--projection-case", action="store_true",
                     help="case study: the small-space projection on the tensor cores and on the CUDA cores, then "
                          "exit without a bench line")
