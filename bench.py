@@ -458,13 +458,15 @@ BATCH_CHARGES = (2.0 / 3.0, -1.0 / 3.0)
 
 
 def batched_case(args):
-    """The batched configuration: 24^3x48, Dirichlet x and t, 12 spin-colour point sources at each
-    of the field values E in --batch-fields (phases q E for q = 2/3, then -1/3, in that order), the
-    --batch-nev lowest |lambda| eigenvectors of Q per phase (eigensolver to 2e-6, an FP32-level
-    bank; each phase after the first warm-started from the nearest bank), minimax polynomial
-    n = 527 on [4e-4, 1], m = 0.02, every right-hand side solved to 1e-10 in one solve_overlap call,
-    in each inner precision of --batch-inner.  Against it: single-source solves of one source per
-    phase.  Prints one JSON object (a case study, not the bench line)."""
+    """The batched configuration (defaults: 24^3x48, links exp(i 0.2 H), minimax n = 527 on
+    [4e-4, 1], m = 0.02; --batch-dims, --batch-link-eps, --batch-degree, --batch-sqrt-eps and
+    --batch-mass change them), Dirichlet x and t, --batch-sources spin-colour point sources (12) at
+    each of the field values E in --batch-fields (phases q E for q = 2/3, then -1/3, in that order;
+    the first --batch-phases of them), the --batch-nev lowest |lambda| eigenvectors of Q per phase
+    (eigensolver to 2e-6, an FP32-level bank; each phase after the first warm-started from the
+    nearest bank), every right-hand side solved to 1e-10 in one solve_overlap call, in each inner
+    precision of --batch-inner.  Against it: single-source solves of one source for each of the
+    first --batch-single phases.  Prints one JSON object (a case study, not the bench line)."""
     import numpy as np
     import torch
 
@@ -503,6 +505,8 @@ def batched_case(args):
                         "lambda_max": float(abs(lam).max()), "info": ctx.last_info})
             print(f"batched_case {inner}: eigensolver phase {ph:.3e}: {eig[-1]['seconds']:.1f} s", flush=True)
         setup_s = time.perf_counter() - t0
+        free, total = torch.cuda.mem_get_info()
+        used_after_eig = (total - free) / 1e9
         b = torch.from_numpy(np.concatenate([b1] * len(phases))).cuda()
         ph_rhs = [ph for ph in phases for _ in range(nsrc)]
         # single-source reference solves (one per phase; the first also times the launch shapes)
@@ -525,6 +529,7 @@ def batched_case(args):
         e1.record()
         torch.cuda.synchronize()
         secs = e0.elapsed_time(e1) / 1e3
+        free, total = torch.cuda.mem_get_info()
         applies = st.dslash_calls / (2 * degree + 1)
         single_per_source = sum(r["seconds"] for r in single) / len(single) if single else float("nan")
         out["runs"][inner] = {
@@ -534,7 +539,8 @@ def batched_case(args):
             "dov_applies_per_s": applies / secs, "dov_applies_per_s_per_rhs": applies / secs / nrhs,
             "outer": st.outer_iters, "inner": st.inner_iters, "sign_applies": st.sign_applies,
             "worst_true_residual": st.true_residual, "cycles": ctx.last_info, "tuning": ctx.tune_info,
-            "single": single}
+            "single": single, "device_gb_in_use": {"after_eigensolver": used_after_eig,
+                                                   "after_solve": (total - free) / 1e9}}
         print(f"batched_case {inner}: {nrhs} rhs in {secs:.1f} s ({secs / nrhs:.2f} s per source, single "
               f"{single_per_source:.2f} s), residual {st.true_residual:.2e}", flush=True)
         ctx.close()

@@ -281,6 +281,14 @@ int deflate(ov_ctx* ctx, double phase, const void* V, const double* lambda, int 
 int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_iter,
                     void* V_out, double* lambda_out, int register_bank, ov_stream_t stream);
 
+/* Working-set budget, in bytes, of ov_eigensolve_Q's chunked passes: its Chebyshev filter runs the
+ * recurrence on as many columns of the block at a time as fit three vectors of the iteration's
+ * precision per column in `bytes` (at least one column), and its residual pass uses chunks of the
+ * same width.  Not counted: the block itself (three sets of m = min(n_ev + max(16, n_ev), 256)
+ * vectors, FP32 while the residuals are above FP32 resolution, FP64 after) and the n_ev FP64 result.
+ * Results do not depend on it beyond rounding.  Default 16e9 (16 GB); bytes >= 1. */
+int ov_set_eigensolver_memory(ov_ctx* ctx, long long bytes);
+
 /* The small-space projection alone (Sec. 2, Fig. 1: the exactly treated low modes), as apply_sign_Hw
  * applies it: with the bank V, s registered for `phase` by deflate(),
  *   xperp = in - V (V^+ in),   ys = V diag(s) (V^+ in)

@@ -99,6 +99,7 @@ _SIGNATURES = {
     "apply_wilson_noalloc": (_I, [C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _VP, _VP, _VP, _I, _DP, _I, _VP]),
     "ov_project_small": (_I, [_VP, _D, _VP, _VP, _VP, _I, _VP]),
     "ov_set_projection": (_I, [_VP, _I]),
+    "ov_set_eigensolver_memory": (_I, [_VP, C.c_longlong]),
     "deflate": (_I, [_VP, _D, _VP, _DP, _I, _I, _VP]),
     "ov_eigensolve_Q": (_I, [_VP, _D, _I, _D, _I, _VP, _DP, _I, _VP]),
     "ov_set_inner_precision": (_I, [_VP, _I]),
@@ -285,6 +286,10 @@ class Context:
     def set_projection(self, method):
         """FP32 small-space projections of 8+ vectors: 0 timed choice, 1 CUDA cores, 2 tensor cores."""
         _check(lib().ov_set_projection(self.handle, int(method)), self.handle)
+
+    def set_eigensolver_memory(self, nbytes):
+        """Working-set budget (bytes) of the eigensolver's chunked filter and residual passes."""
+        _check(lib().ov_set_eigensolver_memory(self.handle, int(nbytes)), self.handle)
 
     def set_profiling(self, on=True):
         """Record CUDA events around every polynomial (Clenshaw) loop."""

@@ -126,6 +126,8 @@ struct ov_ctx {
     // 2 = tensor cores; the timed choice per (bank size, batch)
     int proj_method = 0;
     std::map<std::pair<int, int>, int> proj_choice;
+    // working-set budget of the eigensolver's chunked passes (filter recurrence, residuals)
+    long long eig_chunk_bytes = 16000000000LL;
     Buf tc_img;  // pre-split coefficients of the tensor-core projection
     std::string tune_log;
     cudaStream_t cap_stream = nullptr;
@@ -347,9 +349,12 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-__global__ void random_fill_k(double2* __restrict__ x, long long n, unsigned long long seed) {
+// x[i] from the numbers of elements i0 + i of the sequence (so that a block filled in pieces gets the
+// numbers of one fill)
+__global__ void random_fill_k(double2* __restrict__ x, long long n, unsigned long long seed, long long i0) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long a = splitmix64(seed ^ (2ULL * i)), b = splitmix64(seed ^ (2ULL * i + 1));
+        const unsigned long long k = (unsigned long long)(i0 + i);
+        const unsigned long long a = splitmix64(seed ^ (2ULL * k)), b = splitmix64(seed ^ (2ULL * k + 1));
         x[i] = make_double2((double)(a >> 11) * 0x1.0p-53 - 0.5, (double)(b >> 11) * 0x1.0p-53 - 0.5);
     }
 }
@@ -886,44 +891,57 @@ int register_bank_internal(ov_ctx* c, double phase, const void* W64, int n, cons
     return OV_OK;
 }
 
+// Columns of the eigensolver's block per chunk of its filter and residual passes: three vectors of
+// precision prec per column within the context's budget, at least one column.
+int eig_chunk(const ov_ctx* c, int prec, int m) {
+    const long long per_column = 3LL * (long long)vec_bytes(c, prec);
+    return (int)std::max(1LL, std::min<long long>(m, c->eig_chunk_bytes / per_column));
+}
+
 // Chebyshev filter W <- T_d(Z) W (then normalised by the caller), Z = (2 Q^2 - (1 + a))/(1 - a),
 // which damps the part of the spectrum of Q^2 in [a, 1] and amplifies [0, a).  W: m vectors of
-// precision R.
+// precision R, filtered a chunk of columns at a time (the recurrence acts on each column alone;
+// its three temporaries are chunk-sized).
 template <typename R>
 int cheb_filter(ov_ctx* c, void* W, int m, double a, int degree, const double* d_phase, cudaStream_t s) {
     const int prec = prec_of<R>();
     const size_t vb = vec_bytes(c, prec);
+    const int cw = eig_chunk(c, prec, m);
     void *Tm, *Tc, *tt;
-    TRY(workspace(c, "flt_Tm", prec, m, &Tm));
-    TRY(workspace(c, "flt_Tc", prec, m, &Tc));
-    TRY(workspace(c, "flt_t", prec, m, &tt));
+    TRY(workspace(c, "flt_Tm", prec, cw, &Tm));
+    TRY(workspace(c, "flt_Tc", prec, cw, &Tc));
+    TRY(workspace(c, "flt_t", prec, cw, &tt));
     const double h = c->hw_norm, m0 = c->p.m0;
     const double za = 2.0 / ((1.0 - a) * h * h), zb = -(1.0 + a) / (1.0 - a);
     const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
-    Epilogue plain;
-    launch_dslash<R>(c->g, m0, U, W, tt, m, d_phase, plain, s);
-    Epilogue e1;
-    e1.c_op = za;
-    e1.c1 = zb;
-    e1.v1 = W;
-    launch_dslash<R>(c->g, m0, U, tt, Tc, m, d_phase, e1, s);  // T_1 = Z W
-    CK(cudaMemcpyAsync(Tm, W, vb * m, cudaMemcpyDeviceToDevice, s));  // T_0
-    void* tk = Tc;
-    void* tkm = Tm;
-    for (int k = 1; k < degree; ++k) {
-        launch_dslash<R>(c->g, m0, U, tk, tt, m, d_phase, plain, s);
-        Epilogue e;
-        e.c_op = 2.0 * za;
-        e.c1 = 2.0 * zb;
-        e.v1 = tk;
-        e.c3 = -1.0;
-        e.v3 = tkm;
-        launch_dslash<R>(c->g, m0, U, tt, tkm, m, d_phase, e, s);  // T_{k+1} written over T_{k-1}
-        std::swap(tk, tkm);
+    for (int j0 = 0; j0 < m; j0 += cw) {
+        const int nj = std::min(cw, m - j0);
+        void* Wj = (char*)W + vb * j0;
+        Epilogue plain;
+        launch_dslash<R>(c->g, m0, U, Wj, tt, nj, d_phase, plain, s);
+        Epilogue e1;
+        e1.c_op = za;
+        e1.c1 = zb;
+        e1.v1 = Wj;
+        launch_dslash<R>(c->g, m0, U, tt, Tc, nj, d_phase, e1, s);  // T_1 = Z W
+        CK(cudaMemcpyAsync(Tm, Wj, vb * nj, cudaMemcpyDeviceToDevice, s));  // T_0
+        void* tk = Tc;
+        void* tkm = Tm;
+        for (int k = 1; k < degree; ++k) {
+            launch_dslash<R>(c->g, m0, U, tk, tt, nj, d_phase, plain, s);
+            Epilogue e;
+            e.c_op = 2.0 * za;
+            e.c1 = 2.0 * zb;
+            e.v1 = tk;
+            e.c3 = -1.0;
+            e.v3 = tkm;
+            launch_dslash<R>(c->g, m0, U, tt, tkm, nj, d_phase, e, s);  // T_{k+1} written over T_{k-1}
+            std::swap(tk, tkm);
+        }
+        CKL();
+        CK(cudaMemcpyAsync(Wj, tk, vb * nj, cudaMemcpyDeviceToDevice, s));
     }
-    CKL();
     c->dslash_count += 2LL * degree * m;
-    CK(cudaMemcpyAsync(W, tk, vb * m, cudaMemcpyDeviceToDevice, s));
     return OV_OK;
 }
 
@@ -933,13 +951,15 @@ int cheb_filter(ov_ctx* c, void* W, int m, double a, int degree, const double* d
 // mixtures of +lambda and -lambda eigenvectors (same Q^2, so the filter never separates them)
 // whose Q Rayleigh quotient is near zero.  (2) With Q inside the first n_ev columns: resolves the
 // signs; ordered by |theta|.  On return W (and QW) hold the rotated block, theta the Ritz values
-// of the first n_ev columns and res their squared residuals ||Q w - theta w||^2.
+// of the first n_ev columns and res their squared residuals ||Q w - theta w||^2.  Three sets of m
+// vectors (W, QW and the rotation target W2, whose roles rotate) and a chunk-sized one for the
+// residuals.
 template <typename R>
-int eig_rayleigh_ritz(ov_ctx* c, int m, int n_ev, void*& W, void*& W2, void*& QW, void*& QW2, void* tt,
-                      const double* d_phase, std::vector<double>& theta, std::vector<double>& res, double& a,
-                      cudaStream_t s) {
+int eig_rayleigh_ritz(ov_ctx* c, int m, int n_ev, void*& W, void*& W2, void*& QW, const double* d_phase,
+                      std::vector<double>& theta, std::vector<double>& res, double& a, cudaStream_t s) {
     const long long n12 = 12LL * c->g.V;
-    const size_t vb = vec_bytes(c, prec_of<R>());
+    const int prec = prec_of<R>();
+    const size_t vb = vec_bytes(c, prec);
     const void* U = std::is_same<R, double>::value ? c->U64 : c->U32;
     Epilogue eq;
     eq.c_op = 1.0 / c->hw_norm;
@@ -953,10 +973,13 @@ int eig_rayleigh_ritz(ov_ctx* c, int m, int n_ev, void*& W, void*& W2, void*& QW
         hermitize(G2, m);
         host_eigh(m, G2, mu, Y);
         a = std::min(mu[m - 1], 0.95);
-        TRY(rotate<R>(c, W, m, Y, m, W2, s));
-        TRY(rotate<R>(c, QW, m, Y, m, QW2, s));
-        std::swap(W, W2);
-        std::swap(QW, QW2);
+        void* const w_old = W;
+        void* const qw_old = QW;
+        TRY(rotate<R>(c, W, m, Y, m, W2, s));      // the rotated block
+        TRY(rotate<R>(c, QW, m, Y, m, w_old, s));  // its image, over the old block
+        W = W2;
+        QW = w_old;
+        W2 = qw_old;
     }
     std::vector<HostCplx> T, Z;
     TRY(gram_host<R>(c, W, n_ev, QW, n_ev, T, s));
@@ -973,18 +996,24 @@ int eig_rayleigh_ritz(ov_ctx* c, int m, int n_ev, void*& W, void*& W2, void*& QW
         theta[j] = w[order[j]];
         for (int i = 0; i < n_ev; ++i) Zs[i + (size_t)j * n_ev] = Z[i + (size_t)order[j] * n_ev];
     }
-    // rotate the first n_ev columns in place (through W2/QW2): the block's span is unchanged
+    // rotate the first n_ev columns in place (through W2): the block's span is unchanged
     TRY(rotate<R>(c, W, n_ev, Zs, n_ev, W2, s));
-    TRY(rotate<R>(c, QW, n_ev, Zs, n_ev, QW2, s));
     CK(cudaMemcpyAsync(W, W2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(QW, QW2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
+    TRY(rotate<R>(c, QW, n_ev, Zs, n_ev, W2, s));
+    CK(cudaMemcpyAsync(QW, W2, vb * n_ev, cudaMemcpyDeviceToDevice, s));
     std::vector<double> mth(n_ev), ones(n_ev, 1.0);
     for (int i = 0; i < n_ev; ++i) mth[i] = -theta[i];
-    CK(cudaMemcpyAsync(tt, QW, vb * n_ev, cudaMemcpyDeviceToDevice, s));
-    launch_axpby<R>(mth.data(), W, ones.data(), tt, n12, n_ev, s);
-    CKL();
-    TRY(ensure_small(c, 0, (long long)kRedBlocks * m, m));
-    norm2_rhs<R>(tt, n12, n_ev, res.data(), c->d_partial, c->d_red, s);
+    const int cw = eig_chunk(c, prec, n_ev);
+    void* tt;
+    TRY(workspace(c, "eig_t", prec, cw, &tt));
+    TRY(ensure_small(c, 0, (long long)kRedBlocks * cw, cw));
+    for (int j0 = 0; j0 < n_ev; j0 += cw) {
+        const int nj = std::min(cw, n_ev - j0);
+        CK(cudaMemcpyAsync(tt, (const char*)QW + vb * j0, vb * nj, cudaMemcpyDeviceToDevice, s));
+        launch_axpby<R>(mth.data() + j0, (const char*)W + vb * j0, ones.data() + j0, tt, n12, nj, s);
+        CKL();
+        norm2_rhs<R>(tt, n12, nj, res.data() + j0, c->d_partial, c->d_red, s);
+    }
     return OV_OK;
 }
 
@@ -1224,6 +1253,13 @@ int ov_set_projection(ov_ctx* c, int method) {
     return OV_OK;
 }
 
+int ov_set_eigensolver_memory(ov_ctx* c, long long bytes) {
+    if (!c) return OV_ERR_ARG;
+    if (bytes < 1) return fail(c, OV_ERR_ARG, "eigensolver memory budget = %lld bytes invalid", bytes);
+    c->eig_chunk_bytes = bytes;
+    return OV_OK;
+}
+
 int ov_project_small(ov_ctx* c, double phase, const void* in, void* ys, void* xperp, int nrhs, ov_stream_t stream) {
     if (!c) return OV_ERR_ARG;
     if (!in || !ys || !xperp) return fail(c, OV_ERR_ARG, "null spinor pointer");
@@ -1295,38 +1331,37 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     // wanted set ends in (near-degenerate modes at the cut converge at the rate set by a)
     const int m = std::min(std::min(n_ev + std::max(16, n_ev), 12 * c->g.V), kMaxRhs);
     const long long n12 = 12LL * c->g.V;
+    const size_t vb32 = vec_bytes(c, OV_PREC_F32);
     // the block lives in FP32 while the residuals are well above FP32 resolution (filter,
-    // Cholesky-QR and Rayleigh-Ritz all on FP32 vectors), then in FP64
-    // Memory: the FP32 block (five sets of m vectors, plus three in the filter) lives until the switch
-    // to FP64, the FP64 block from then on; both are released when the call returns.
-    void *W, *W2 = nullptr, *QW = nullptr, *QW2 = nullptr, *tt = nullptr, *Wf, *W2f, *QWf, *QW2f, *ttf;
-    TRY(workspace(c, "eig_W", OV_PREC_F64, m, &W));
-    auto f64_block = [&]() -> int {
-        TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
-        TRY(workspace(c, "eig_QW", OV_PREC_F64, m, &QW));
-        TRY(workspace(c, "eig_QW2", OV_PREC_F64, m, &QW2));
-        TRY(workspace(c, "eig_t", OV_PREC_F64, m, &tt));
-        return OV_OK;
-    };
+    // Cholesky-QR and Rayleigh-Ritz all on FP32 vectors), then in FP64.
+    // Memory: three sets of m vectors (block, image under Q, rotation target) in FP32 until the
+    // switch to FP64 and in FP64 after it, chunk-sized sets for the filter and the residuals, and at
+    // the end the n_ev wanted vectors in FP64; all released when the call returns.
+    void *W = nullptr, *W2 = nullptr, *QW = nullptr, *Wf, *W2f, *QWf;
     TRY(workspace(c, "eig_W", OV_PREC_F32, m, &Wf));
     TRY(workspace(c, "eig_W2", OV_PREC_F32, m, &W2f));
     TRY(workspace(c, "eig_QW", OV_PREC_F32, m, &QWf));
-    TRY(workspace(c, "eig_QW2", OV_PREC_F32, m, &QW2f));
-    TRY(workspace(c, "eig_t", OV_PREC_F32, m, &ttf));
-    random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)W, n12 * m, 0x5eed0f0e1ULL);
-    count_launch();
-    CKL();
+    {  // random start block, drawn in FP64 a chunk of columns at a time
+        const int cw = eig_chunk(c, OV_PREC_F64, m);
+        void* r64;
+        TRY(workspace(c, "eig_r", OV_PREC_F64, cw, &r64));
+        for (int j0 = 0; j0 < m; j0 += cw) {
+            const int nj = std::min(cw, m - j0);
+            random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)r64, n12 * nj, 0x5eed0f0e1ULL, n12 * j0);
+            count_launch();
+            launch_convert<double, float>(r64, (char*)Wf + vb32 * j0, c->g.V, nj, s);
+        }
+        CKL();
+        TRY(release_workspaces(c, "eig_r/", s));
+    }
     // warm start: the bank of the nearest other field phase, if one is registered, replaces the first
     // random vectors (the field moves the low modes of Q little at the phases of the background-field
-    // method, so the filter then only has to correct them)
+    // method, so the filter then only has to correct them); its FP32 copy is its FP64 vectors rounded
     const Bank* warm = nullptr;
     for (const Bank& bk : c->banks)
         if (bk.n > 0 && bk.phase != phase && (!warm || std::fabs(bk.phase - phase) < std::fabs(warm->phase - phase)))
             warm = &bk;
-    if (warm)
-        CK(cudaMemcpyAsync(W, warm->V64, vec_bytes(c, OV_PREC_F64) * std::min(warm->n, m), cudaMemcpyDeviceToDevice, s));
-    launch_convert<double, float>(W, Wf, c->g.V, m, s);
-    CKL();
+    if (warm) CK(cudaMemcpyAsync(Wf, warm->V32, vb32 * std::min(warm->n, m), cudaMemcpyDeviceToDevice, s));
     TRY(cholqr2<float>(c, Wf, m, W2f, s));
     SysSet S;
     S.n = m;
@@ -1355,12 +1390,13 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
         if (it > 0) {
             if (!in_f64 && (worst <= switch_res || (switch_res > 0.0 && worst < 1e-4 && worst > 0.9 * prev_worst))) {
                 // FP32 -> FP64: widen the block and restore FP64 orthonormality
+                TRY(workspace(c, "eig_W", OV_PREC_F64, m, &W));
                 launch_convert<float, double>(Wf, W, c->g.V, m, s);
                 CKL();
                 TRY(release_workspaces(c, "flt_", s));
-                TRY(release_workspaces(c, "eig_W/32", s));
-                for (const char* nm : {"eig_W2/32", "eig_QW/32", "eig_QW2/32", "eig_t/32"}) TRY(release_workspaces(c, nm, s));
-                TRY(f64_block());
+                for (const char* nm : {"eig_W/32", "eig_W2/32", "eig_QW/32", "eig_t/32"}) TRY(release_workspaces(c, nm, s));
+                TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
+                TRY(workspace(c, "eig_QW", OV_PREC_F64, m, &QW));
                 auto t0 = std::chrono::steady_clock::now();
                 TRY(cholqr2<double>(c, W, m, W2, s));
                 t_ortho += since(t0);
@@ -1381,8 +1417,8 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
             t_ortho += since(to);
         }
         const auto t_rr0 = std::chrono::steady_clock::now();
-        if (in_f64) TRY(eig_rayleigh_ritz<double>(c, m, n_ev, W, W2, QW, QW2, tt, d_phase, theta, res, a, s));
-        else TRY(eig_rayleigh_ritz<float>(c, m, n_ev, Wf, W2f, QWf, QW2f, ttf, d_phase, theta, res, a, s));
+        if (in_f64) TRY(eig_rayleigh_ritz<double>(c, m, n_ev, W, W2, QW, d_phase, theta, res, a, s));
+        else TRY(eig_rayleigh_ritz<float>(c, m, n_ev, Wf, W2f, QWf, d_phase, theta, res, a, s));
         t_rr += since(t_rr0);
         worst = 0.0;
         for (int i = 0; i < n_ev; ++i) worst = std::max(worst, std::sqrt(res[i]));
@@ -1395,13 +1431,17 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
             break;
         }
     }
-    if (!in_f64) {  // converged (or stopped) in FP32: hand out FP64 vectors
-        launch_convert<float, double>(Wf, W, c->g.V, m, s);
-        CKL();
+    if (!in_f64) {  // converged (or stopped) in FP32: hand out the n_ev wanted vectors in FP64,
+                    // orthonormalised in FP64 (the first n_ev columns of a Cholesky-QR of the block)
         TRY(release_workspaces(c, "flt_", s));
-        for (const char* nm : {"eig_W2/32", "eig_QW/32", "eig_QW2/32", "eig_t/32"}) TRY(release_workspaces(c, nm, s));
-        TRY(workspace(c, "eig_W2", OV_PREC_F64, m, &W2));
-        TRY(cholqr2<double>(c, W, m, W2, s));
+        TRY(release_workspaces(c, "eig_t/32", s));
+        TRY(workspace(c, "eig_W", OV_PREC_F64, n_ev, &W));
+        launch_convert<float, double>(Wf, W, c->g.V, n_ev, s);
+        CKL();
+        for (const char* nm : {"eig_W/32", "eig_W2/32", "eig_QW/32"}) TRY(release_workspaces(c, nm, s));
+        TRY(workspace(c, "eig_W2", OV_PREC_F64, n_ev, &W2));
+        TRY(cholqr2<double>(c, W, n_ev, W2, s));
+        TRY(release_workspaces(c, "eig_W2/64", s));
     }
     for (int i = 0; i < n_ev; ++i) lambda_out[i] = theta[i];
     if (V_out) {
@@ -1410,8 +1450,7 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
     }
     if (register_bank && status == OV_OK) TRY(register_bank_internal(c, phase, W, n_ev, theta.data(), s));
     CK(cudaStreamSynchronize(s));
-    // the block's ten workspaces (2 n_ev vectors each in FP64 and FP32) are the largest the library
-    // holds; they serve only this call
+    // the block's workspaces are the largest the library holds; they serve only this call
     TRY(release_workspaces(c, "eig_", s));
     TRY(release_workspaces(c, "flt_", s));
     if (take_timeouts() > 0) return fail(c, OV_ERR_TIMEOUT, "eigensolver: a bounded device wait ran out");
@@ -1604,7 +1643,7 @@ int lanczos_overlap(ov_ctx* c, double phase, int chi, int n_ev, int K, double to
     S1.chi = {(signed char)chi};
     TRY(ensure_small(c, (long long)(K + 1) * std::max(K, n_ev), (long long)(K + 1) * 4 * 152, std::max(n_ev, 1)));
     // start: a random vector of the sector, normalised
-    random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)r64, n12, 0x1a2c3e5dULL + (unsigned long long)(chi + 2));
+    random_fill_k<<<152 * 8, 256, 0, s>>>((double2*)r64, n12, 0x1a2c3e5dULL + (unsigned long long)(chi + 2), 0);
     count_launch();
     launch_convert<double, float>(r64, t, V, 1, s);
     const int zero = 0;

@@ -207,6 +207,10 @@ def test_newer_calls_check_their_arguments_on_the_host(ovl):
     assert L.ov_clear_overlap_deflation(h, 0.0, 0) == 0  # nothing registered: nothing to free
     assert L.ov_clear_overlap_deflation(None, 0.0, 0) == 1
     assert L.ov_eigensolve_overlap(None, 0.0, 1, 4, 0, 1e-4, 5, theta, res, None) == 1
+    assert L.ov_set_eigensolver_memory(h, 0) == 1
+    assert L.ov_set_eigensolver_memory(h, -5) == 1
+    assert L.ov_set_eigensolver_memory(h, 1) == 0
+    assert L.ov_set_eigensolver_memory(None, 1 << 34) == 1
     L.ov_destroy(h)
     out = (ctypes.c_double * 8)()
     assert L.ov_minimax_coeffs(-1, 0.01, out) < 0
