@@ -142,7 +142,7 @@ def config3_small():
         H = dense.hw_matrix(U, M0, obc, phase)
         lam, W, lam_all, _ = dense.low_modes(H, hw, n_ev)
         banks[phase] = (lam, dense.vectors_to_fields(W, synth.site_shape(dims)))
-        cut.append(np.sort(np.abs(lam_all / hw))[n_ev])
+        cut.append(np.sort(np.abs(lam_all))[n_ev])
     eps = (0.9 * min(cut)) ** 2
     return dict(dims=dims, bc=bc, obc=obc, U=U, hw=hw, banks=banks, eps=eps)
 
@@ -173,6 +173,61 @@ def test_config3_shape_batched_solve_against_oracle(P, config3_small, inner):
     for j in range(24):
         lam, V = d["banks"][phases[j]]
         p = ov.OverlapParams(m0=M0, hw_norm=d["hw"], eps=d["eps"], degree=degree, bc=d["obc"])
+        r = b[j] - ov.overlap(d["U"], xs[j], mass, p, ov.SmallSpace.from_eigenpairs(V, lam), phases[j])
+        assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol, j
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def config5_small():
+    """The largest configuration's parameters on 4 x 4 x 2 x 4: links exp(i 0.15 H), Dirichlet x and
+    t, sqrt(eps) = 0.01 and the minimax polynomial of degree 1054 (delta 1.2e-10), five field
+    phases, and per phase the 12 lowest |lambda| eigenvectors of Q from the oracle's dense spectrum
+    (the surface modes, |lambda| from 4.5e-3 to 0.038; the rest of each spectrum lies above 0.043,
+    inside [sqrt(eps), 1])."""
+    from oracle import chebyshev
+
+    dims, bc = (4, 4, 2, 4), (2, 0, 0, 2)
+    obc = (0.0, 1.0, 1.0, 0.0)
+    U = synth.random_su3_field(dims, 0.15, 0)
+    hw, n_ev, eps, degree = 6.5, 12, 1e-4, 1054
+    banks = {}
+    for phase in (0.0, 0.1, -0.1, 0.2, 0.3):
+        lam, W, lam_all, _ = dense.low_modes(dense.hw_matrix(U, M0, obc, phase), hw, n_ev)
+        assert np.sort(np.abs(lam_all))[n_ev] > np.sqrt(eps)
+        banks[phase] = (lam, dense.vectors_to_fields(W, synth.site_shape(dims)))
+    coeffs, delta = chebyshev.minimax_coeffs(degree, eps)
+    return dict(dims=dims, bc=bc, obc=obc, U=U, hw=hw, banks=banks, eps=eps, degree=degree, coeffs=coeffs,
+                delta=delta)
+
+
+def test_config5_shape_batched_solve_against_oracle(P, config5_small):
+    """12 spin-colour point sources x 5 field phases in one solve_overlap call (60 right-hand sides,
+    120 chiral systems), m = 0.01, tol 1e-10, the degree-1054 minimax polynomial on [1e-4, 1],
+    adaptive order, FP32 inner CG.  The library's FP64 residual of every column meets the tolerance;
+    two columns per phase (spin-colour 0 and 11) are checked with the oracle's D(m), each about 2100
+    oracle Wilson applications."""
+    import torch
+
+    d, mass, tol = config5_small, 0.01, 1e-10
+    assert d["delta"] < 2e-10
+    ctx = P.Context(P.Params(dims=d["dims"], bc=d["bc"], m0=M0, eps=d["eps"], poly_degree=d["degree"],
+                             poly_kind=1, precision=P.OV_PREC_F32, inner_precision=P.OV_PREC_F32, max_nrhs=60,
+                             adaptive_order=1))
+    ctx.set_gauge(dev(d["U"]))
+    phases = []
+    for phase, (lam, V) in d["banks"].items():
+        P.deflate(ctx, dev(V), lam, phase=phase)
+        phases += [phase] * 12
+    b = np.concatenate([synth.point_sources(d["dims"])] * 5)
+    x = torch.zeros_like(dev(b))
+    st = P.solve_overlap(ctx, dev(b), x, mass, tol=tol, phase=phases)
+    print(f"{st.outer_iters} outer, {st.inner_iters} inner; {ctx.last_info}")
+    assert st.status == 0 and st.true_residual <= tol
+    xs = x.cpu().numpy()
+    p = ov.OverlapParams(m0=M0, hw_norm=d["hw"], eps=d["eps"], degree=d["degree"], bc=d["obc"], coeffs=d["coeffs"])
+    for j in [k for ph in range(5) for k in (12 * ph, 12 * ph + 11)]:
+        lam, V = d["banks"][phases[j]]
         r = b[j] - ov.overlap(d["U"], xs[j], mass, p, ov.SmallSpace.from_eigenpairs(V, lam), phases[j])
         assert np.linalg.norm(r) / np.linalg.norm(b[j]) <= 2 * tol, j
     ctx.close()
