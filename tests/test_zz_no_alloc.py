@@ -7,8 +7,8 @@ device synchronisation cudaMalloc and cudaFree can cause): it works in one
 fixed file-scope device array instead of allocating.
 These checks run two calls in a row on different lattices and inputs (so the
 second call starts from the first call's leftovers in the shared array) and
-compare each with apply_wilson, the context-based entry point, to the FP64
-tolerance of the other parity tests.  The file sorts last so that a run that
+compare each with apply_wilson, the context-based entry point, and with the
+oracle's Wilson operator, to the FP64 tolerance of the other parity tests.  The file sorts last so that a run that
 stops at the first failure has run every other test before it.
 """
 from __future__ import annotations
@@ -19,11 +19,13 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import dirac
 
 pytestmark = pytest.mark.gpu
 
 F64_TOL = 1e-12
 M0 = -1.5
+BC_NUM = {0: 1.0, 1: -1.0, 2: 0.0}  # periodic, antiperiodic, Dirichlet (as factors on the boundary hop)
 
 
 @pytest.fixture(scope="module")
@@ -83,6 +85,10 @@ def test_noalloc_matches_apply_wilson_on_two_calls_in_a_row(P):
         got = noalloc(P, dims, bc, U, x, phases, herm)
         assert np.all(np.isfinite(got))
         assert relerr(got, want) < F64_TOL
+        op = dirac.hermitian_wilson if herm else dirac.wilson
+        obc = tuple(BC_NUM[v] for v in bc)
+        for j, ph in enumerate(phases):
+            assert relerr(got[j], op(U, x[j], M0, obc, ph)) < F64_TOL
 
 
 def test_noalloc_rejects_requests_beyond_its_array(P):
