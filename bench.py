@@ -57,7 +57,8 @@ WORKLOAD = f"16^3x32 deflated overlap point-source solve, n={DEGREE}, N_ev={N_EV
 # the kernel case (cold caches).  When the kernel source changes the ratios are stale and `traffic`
 # is reported as null until they are measured again.
 KERNEL_SHA = "f7f9e39adeb0aa18"
-DRAM_OVER_ALGORITHMIC = {"f32_16x16x16x32_solve": 0.09, "f32_24x24x24x48": 0.87}
+DRAM_OVER_ALGORITHMIC = {"f32_16x16x16x32_solve": 0.09, "f32_24x24x24x48": 0.87, "f16_24x24x24x48": 0.83,
+                         "bf16_24x24x24x48": 0.83}
 HBM_DIMS = (24, 24, 24, 48)  # the HBM-bound case: links and vectors far beyond the 129 MB L2
 
 
