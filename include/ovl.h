@@ -277,7 +277,9 @@ int deflate(ov_ctx* ctx, double phase, const void* V, const double* lambda, int 
  * another phase, the iteration starts from that bank's vectors (the nearest phase's; random vectors
  * fill the rest of the block).  If register_bank is
  * non-zero the result is also registered as by deflate().  Returns OV_ERR_NOT_CONVERGED
- * (with the best vectors written) after max_iter filter cycles. */
+ * (with the best vectors written) after max_iter filter cycles.  The call's block and filter
+ * workspaces (the largest allocations of the library) are freed when it returns, also when it
+ * fails part-way (OV_ERR_OOM, OV_ERR_CUDA, OV_ERR_BREAKDOWN). */
 int ov_eigensolve_Q(ov_ctx* ctx, double phase, int n_ev, double tol, int max_iter,
                     void* V_out, double* lambda_out, int register_bank, ov_stream_t stream);
 

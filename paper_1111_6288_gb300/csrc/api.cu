@@ -227,6 +227,20 @@ int release_workspaces(ov_ctx* c, const std::string& prefix, cudaStream_t s) {
     return OV_OK;
 }
 
+// The same after a failed call: the stream's error (already reported) is not checked again, and the
+// buffers leave the context even if freeing them fails.
+void release_workspaces_after_error(ov_ctx* c, const std::string& prefix, cudaStream_t s) {
+    cudaStreamSynchronize(s);
+    for (auto it = c->ws.begin(); it != c->ws.end();) {
+        if (it->first.compare(0, prefix.size(), prefix) == 0) {
+            if (it->second.ptr) cudaFree(it->second.ptr);
+            it = c->ws.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 int ensure_small(ov_ctx* c, long long nmat, long long npartial, int nsys) {
     if (nmat > c->cap_c) {
         if (c->d_C) {
@@ -1318,8 +1332,8 @@ int deflate(ov_ctx* c, double phase, const void* V, const double* lambda, int n_
     return register_bank_internal(c, phase, W, n_ev, lambda, s);
 }
 
-int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter, void* V_out, double* lambda_out,
-                    int register_bank, ov_stream_t stream) {
+static int eigensolve_q_body(ov_ctx* c, double phase, int n_ev, double tol, int max_iter, void* V_out,
+                             double* lambda_out, int register_bank, ov_stream_t stream) {
     if (!c) return OV_ERR_ARG;
     if (!c->gauge_set) return fail(c, OV_ERR_STATE, "no gauge field set");
     if (n_ev < 1 || n_ev > 200) return fail(c, OV_ERR_ARG, "n_ev = %d outside [1, 200]", n_ev);
@@ -1467,6 +1481,17 @@ int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter,
         return fail(c, status, "eigensolver: not converged after %d filter cycles; worst residual per cycle: %s",
                     max_iter, hist.c_str());
     return OV_OK;
+}
+
+int ov_eigensolve_Q(ov_ctx* c, double phase, int n_ev, double tol, int max_iter, void* V_out, double* lambda_out,
+                    int register_bank, ov_stream_t stream) {
+    const int rc = eigensolve_q_body(c, phase, n_ev, tol, max_iter, V_out, lambda_out, register_bank, stream);
+    // a call that failed part-way (out of memory, a CUDA error) gives its block back as well
+    if (c && rc != OV_OK && rc != OV_ERR_NOT_CONVERGED) {
+        release_workspaces_after_error(c, "eig_", (cudaStream_t)stream);
+        release_workspaces_after_error(c, "flt_", (cudaStream_t)stream);
+    }
+    return rc;
 }
 
 }  // extern "C"
