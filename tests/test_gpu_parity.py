@@ -352,6 +352,33 @@ def test_eigensolver_in_column_chunks_matches_dense(P, lat4):
     ctx.close()
 
 
+def test_eigensolver_fp32_level_target_with_warm_start(P, lat4):
+    """A target of 2e-6 keeps the whole iteration in FP32; the n_ev wanted vectors are widened to FP64
+    and orthonormalised there.  A second field phase then starts from the first phase's bank.  Both
+    in ragged chunks of 5 columns, against the oracle's dense spectrum and Wilson operator at that
+    phase: eigenvalues to FP32 level, residuals within the target plus the FP64 re-orthonormalisation
+    (FP32 rounding of the vectors, ~1e-7), and FP64-orthonormal vectors."""
+    d = lat4
+    ctx = make_ctx(P, d["dims"], d["bc"])
+    ctx.set_gauge(to_dev(d["U"]))
+    ctx.set_eigensolver_memory(3 * 5 * 12 * int(np.prod(d["dims"])) * 8)
+    for phase in (0.0, 0.2):
+        lam, V = P.eigensolve_Q(ctx, 8, phase=phase, tol=2e-6, max_iter=300, want_vectors=True)
+        info = ctx.last_info
+        assert "f64/" not in info, info
+        assert ("warm start" in info) == (phase != 0.0), info
+        H = dense.hw_matrix(d["U"], M0, oracle_bc(d["bc"]), phase)
+        want, _, _, _ = dense.low_modes(H, d["hw"], 8)
+        assert np.allclose(np.sort(lam), np.sort(want), atol=1e-6), (lam, want)
+        Vh = V.cpu().numpy()
+        G = np.array([[dirac.inner(Vh[i], Vh[j]) for j in range(8)] for i in range(8)])
+        assert np.abs(G - np.eye(8)).max() < 1e-12
+        for i in range(8):
+            r = dirac.hermitian_wilson(d["U"], Vh[i], M0, oracle_bc(d["bc"]), phase) / d["hw"] - lam[i] * Vh[i]
+            assert np.linalg.norm(r) < 3e-6, (phase, i, np.linalg.norm(r))
+    ctx.close()
+
+
 # ---------------------------------------------------------------------------
 # sign function at the measured workload's polynomial (n = 527, sqrt(eps) = 0.02)
 # ---------------------------------------------------------------------------
