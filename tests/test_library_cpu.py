@@ -44,6 +44,22 @@ def test_header_declares_the_entry_points():
         assert want in names
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the public header compiles as strict C99 (plain pointers, sizes and
+    enums; no C++ or framework types)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "uses_ovl.c"
+    src.write_text('#include "include/ovl.h"\nint main(void) { return OV_OK; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", ROOT, "-c", str(src),
+                        "-o", str(tmp_path / "uses_ovl.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol(ovl):
     L = ctypes.CDLL(ovl.library_path())
     missing = [n for n in declared_functions() if not hasattr(L, n)]
